@@ -1,0 +1,217 @@
+"""Whole-scheme pins of the CPU checker: reconstruction exactness, free-stream
+preservation, conservation, convergence order on the exact density wave and
+consistency with the paper's accuracy table (Section 5.1)."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2407_00656_b300 import inputs as I
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def tet_rule(n):
+    """Collapsed-coordinate (conical product) Gauss rule on the unit simplex:
+    barycentric lambda[q,3] and weights summing to 1/6."""
+    x, w = np.polynomial.legendre.leggauss(n)
+    x = 0.5 * (x + 1)
+    w = 0.5 * w
+    S, T, U = np.meshgrid(x, x, x, indexing="ij")
+    W = (w[:, None, None] * w[None, :, None] * w[None, None, :]) * (1 - S) ** 2 * (1 - T)
+    l1 = S
+    l2 = T * (1 - S)
+    l3 = U * (1 - S) * (1 - T)
+    return np.stack([l1.ravel(), l2.ravel(), l3.ravel()], axis=1), W.ravel()
+
+
+def tet_average(xyz, cells, f, n=10):
+    lam, w = tet_rule(n)
+    p = xyz[cells]  # [nc,4,3]
+    e = p[:, 1:] - p[:, :1]  # [nc,3,3]
+    pts = p[:, None, 0, :] + np.einsum("qk,ckd->cqd", lam, e)
+    return 6.0 * np.einsum("q,cq...->c...", w, f(pts))
+
+
+# ---------------------------------------------------------------------------
+# inputs
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("jit", [0.0, 0.15])
+def test_kuhn_mesh_volumes(jit):
+    xyz, cells, per = I.kuhn_cube(4, jitter=jit, seed=3)
+    p = xyz[cells]
+    det = np.einsum("ij,ij->i", np.cross(p[:, 1] - p[:, 0], p[:, 2] - p[:, 0]), p[:, 3] - p[:, 0])
+    assert det.min() > 0
+    assert abs(det.sum() / 6 - 8.0) < 1e-12
+    o = oracle.Oracle(xyz, cells, per)
+    vol = o.geometry()[0]
+    assert np.allclose(vol, det / 6, rtol=1e-13)
+    assert o.n_faces == 2 * len(cells)
+
+
+def test_exact_tet_average_matches_quadrature():
+    xyz, cells, per = I.kuhn_cube(8, jitter=0.15, seed=2)
+    t = 0.37
+    a = I.tet_average_sin(xyz, cells, t)
+    b = tet_average(xyz, cells, lambda x: np.sin(np.pi * (x.sum(-1) - t)), n=12)
+    assert np.abs(a - b).max() < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# reconstruction (Section 2.3)
+# ---------------------------------------------------------------------------
+def _unshifted_cells(o, nmax=40):
+    """Cells whose stencil members are all un-shifted interior cells."""
+    _, cen, _, _ = o.geometry()
+    out = []
+    for c in range(o.n_cells):
+        kind, ids, scen, M = o.stencil(c)
+        if np.all(kind == 0) and np.allclose(scen, cen[ids], atol=1e-12):
+            out.append(c)
+        if len(out) >= nmax:
+            break
+    return out
+
+
+def test_linear_field_reconstructed_exactly():
+    xyz, cells, per = I.kuhn_cube(6, jitter=0.15, seed=4)
+    o = oracle.Oracle(xyz, cells, per)
+    _, cen, _, _ = o.geometry()
+    rng = np.random.default_rng(0)
+    G = rng.normal(size=(5, 3))
+    c0 = rng.normal(size=5)
+    o.set_state(c0[None, :] + cen @ G.T)  # average of a linear field = centroid value
+    o.reconstruct()
+    cells_ok = _unshifted_cells(o)
+    assert len(cells_ok) >= 10
+    for c in cells_ok:
+        x = cen[c] + rng.uniform(-0.1, 0.1, 3)
+        val, grad = o.recon_eval(c, x)
+        assert np.allclose(val, c0 + G @ x, atol=1e-12)
+        assert np.allclose(grad, G, atol=1e-11)
+
+
+def test_quadratic_field_exact_with_linear_weights():
+    xyz, cells, per = I.kuhn_cube(6, jitter=0.15, seed=5)
+    o = oracle.Oracle(xyz, cells, per)
+    _, cen, _, _ = o.geometry()
+    rng = np.random.default_rng(1)
+    A = rng.normal(size=(5, 3, 3))
+    A = A + A.transpose(0, 2, 1)
+    G = rng.normal(size=(5, 3))
+
+    def f(x):
+        return np.einsum("...i,vij,...j->...v", x, A, x) + np.einsum("vi,...i->...v", G, x)
+
+    o.set_state(tet_average(xyz, cells, f, n=6))
+    o.reconstruct(force_linear=True)
+    for c in _unshifted_cells(o):
+        x = cen[c] + rng.uniform(-0.1, 0.1, 3)
+        val, grad = o.recon_eval(c, x)
+        assert np.allclose(val, f(x), atol=1e-11)
+        assert np.allclose(grad, 2 * np.einsum("vij,j->vi", A, x) + G, atol=1e-10)
+
+
+def test_uniform_data_gives_linear_weights_and_mean_is_kept():
+    xyz, cells, per = I.kuhn_cube(4, jitter=0.15, seed=6)
+    o = oracle.Oracle(xyz, cells, per)
+    o.set_state(I.uniform_state(len(cells), 1.2, (0.3, -0.1, 0.2), 0.9))
+    o.reconstruct()
+    w = o.recon_weights(0)
+    assert np.array_equal(w[:, 0], np.full(5, 1 - 0.025 * 4))
+    assert np.array_equal(w[:, 1:], np.full((5, 4), 0.025))
+    # cell mean of the reconstructed polynomial equals the cell average
+    q = I.random_smooth_state(xyz, cells, seed=1)
+    o.set_state(q)
+    o.reconstruct()
+    lam, wq = tet_rule(4)
+    for c in range(0, len(cells), 37):
+        p = xyz[cells[c]]
+        pts = p[0] + lam @ (p[1:] - p[0])
+        mean = 6.0 * sum(wi * o.recon_eval(c, x)[0] for wi, x in zip(wq, pts))
+        assert np.allclose(mean, q[c], atol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# whole scheme
+# ---------------------------------------------------------------------------
+def test_free_stream_preserved_on_jittered_tets(oracle_threads):
+    xyz, cells, per = I.kuhn_cube(5, jitter=0.15, seed=7)
+    o = oracle.Oracle(xyz, cells, per)
+    q = I.uniform_state(len(cells), 1.1, (0.4, -0.3, 0.2), 0.8)
+    o.set_state(q)
+    o.step(2)
+    q2, t, s = o.get_state()
+    assert s == 2 and t > 0
+    assert np.abs(q2 - q).max() < 1e-13
+
+
+@pytest.mark.parametrize("mu", [0.0, 1e-3])
+def test_free_stream_preserved_on_far_field_shell(oracle_threads, mu):
+    xyz, cells, bfn, bft = I.sphere_shell(4, 3, r_far=3.0, jitter=0.1, seed=1)
+    bft = np.full_like(bft, I.BC_FARFIELD)
+    qinf = I.free_stream(0.2535)
+    o = oracle.Oracle(xyz, cells, None, bfn, bft, qinf=qinf, mu_ref=mu, Pr=0.72, visc_exp=0.7, T_ref=1 / 1.4)
+    q = np.tile(qinf, (len(cells), 1))
+    o.set_state(q)
+    o.step(2)
+    q2, _, _ = o.get_state()
+    assert np.abs(q2 - q).max() < 1e-13
+
+
+def test_conservation_on_periodic_mesh(oracle_threads):
+    xyz, cells, per = I.kuhn_cube(5, jitter=0.15, seed=8)
+    o = oracle.Oracle(xyz, cells, per, mu_ref=2e-3, Pr=0.72, tau_c=1.0)
+    vol = o.geometry()[0]
+    q = I.random_smooth_state(xyz, cells, seed=3)
+    o.set_state(q)
+    tot0 = (q * vol[:, None]).sum(axis=0)
+    o.step(3)
+    q3, _, _ = o.get_state()
+    tot3 = (q3 * vol[:, None]).sum(axis=0)
+    assert np.abs(q3 - q).max() > 1e-4  # the state did evolve
+    assert np.all(np.abs(tot3 - tot0) <= 1e-13 * np.abs(tot0).max())
+
+
+def test_wall_shell_runs_and_stays_physical(oracle_threads):
+    xyz, cells, bfn, bft = I.sphere_shell(4, 4, r_far=4.0)
+    qinf = I.free_stream(0.2535)
+    o = oracle.Oracle(xyz, cells, None, bfn, bft, qinf=qinf, mu_ref=0.2535 / 300, Pr=0.72, visc_exp=0.7,
+                      T_ref=1 / 1.4, tau_c=1.0)
+    o.set_state(np.tile(qinf, (len(cells), 1)))
+    o.step(3)
+    q, t, s = o.get_state()
+    assert s == 3 and np.all(np.isfinite(q)) and q[:, 0].min() > 0.9
+
+
+def _wave_error(n, t_end):
+    xyz, cells, per = I.kuhn_cube(n)
+    o = oracle.Oracle(xyz, cells, per)
+    o.set_state(I.density_wave_state(xyz, cells, 0.0))
+    while o.get_state()[1] < t_end:
+        o.step(10, t_end=t_end)
+    q, t, _ = o.get_state()
+    vol = o.geometry()[0]
+    e = np.abs(q[:, 0] - I.density_wave_state(xyz, cells, t)[:, 0])
+    return (e * vol).sum() / vol.sum(), np.sqrt((e * e * vol).sum()) / vol.sum()
+
+
+@pytest.mark.slow
+def test_convergence_order_density_wave(oracle_threads):
+    e8, _ = _wave_error(8, 0.1)
+    e16, _ = _wave_error(16, 0.1)
+    order = np.log2(e8 / e16)
+    assert 2.6 < order < 3.4, order
+
+
+@pytest.mark.slow
+def test_paper_accuracy_table_consistency(oracle_threads):
+    """Soft check of the readings: L1 and L2 errors of rho at N=10, t=2 within
+    25% of the paper's table (the L2 norm normalised as sqrt(sum e^2|cell|)/|domain|,
+    which reproduces the paper's L2/L1 ratio)."""
+    rows = [l.split() for l in open(os.path.join(HERE, "golden", "paper_tet_accuracy.txt")) if l[0] != "#"]
+    paper = {int(r[0]): (float(r[1]), float(r[3])) for r in rows}
+    L1, L2 = _wave_error(10, 2.0)
+    assert abs(L1 / paper[10][0] - 1) < 0.25, (L1, paper[10][0])
+    assert abs(L2 / paper[10][1] - 1) < 0.25, (L2, paper[10][1])
