@@ -1,0 +1,264 @@
+"""Benchmark of the HGKS hot path on one B300 (replicas on N GPUs).
+
+Default workload: the jittered density-wave mesh of 48^3 cubes x 6 tetrahedra
+(663,552 cells), inviscid, FP64, CFL 0.4.  One bench "step" is one full S2O4
+step (time step, two stages of reconstruction, flux and update) of the whole
+mesh.  Metric: cell-updates/s = cells x steps / device time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hgks|reference]
+                    [--precision fp64|mixed] [--workload density48|density24|sphere]
+
+Prints one JSON line (rank 0).  For N > 1 (torchrun) every rank advances its
+own replica of the workload: the path has no exchange step on one GPU per
+problem, so the job is weak-scaled replicas with no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# Executed binary64 operations per face of the flux kernel and per cell of
+# the reconstruction kernel (FP64 path), counted by ncu on the kernels as
+# built (sass dadd + dmul + 2 dfma per launch, divided by the faces or cells
+# of the launch); see profiles/flux_fp64_density12.md.  None until measured.
+FP64_FLOPS_PER_FACE_INVISCID = None
+FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12  # SMs x DFMA/clk x 2 flop x max SM clock
+
+
+def workload(name: str):
+    from paper_2407_00656_b300 import inputs as I
+
+    if name in ("density48", "density24", "density12", "density8"):
+        n = int(name[len("density"):])
+        jit = 0.15 if n != 8 else 0.0
+        xyz, cells, per = I.kuhn_cube(n, jitter=jit, seed=0)
+        q = I.density_wave_state(xyz, cells, 0.0)
+        return dict(xyz=xyz, cells=cells, periods=per, q=q, params={},
+                    desc=f"density wave, {n}^3 x 6 tets" + (", jitter 0.15h seed 0" if jit else "") + ", inviscid")
+    if name == "sphere":
+        xyz, cells, bfn, bft = I.sphere_shell(58, 75, seed=0)
+        qinf = I.free_stream(0.2535)
+        q = np.tile(qinf, (len(cells), 1))
+        return dict(xyz=xyz, cells=cells, periods=None, bfn=bfn, bft=bft, q=q,
+                    params=dict(q_inf=qinf, mu_ref=0.2535 / 300, Pr=0.72, visc_exp=0.7, T_ref=1 / 1.4, tau_num_c=1.0),
+                    desc="sphere shell 6x58^2x75 hex, Ma 0.2535 Re 300, wall + far field")
+    raise ValueError(name)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                if out.returncode == 0 and out.stdout.strip():
+                    self.rows.append([x.strip() for x in out.stdout.strip().split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 5 + i and r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def cpu_baseline(w, budget_steps: int = 1):
+    """The CPU checker as it stands, all host cores, on one step of the same mesh."""
+    import oracle
+
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    o = oracle.Oracle(w["xyz"], w["cells"], w["periods"], w.get("bfn"), w.get("bft"),
+                      **{{"tau_num_c": "tau_c", "q_inf": "qinf"}.get(k, k): v for k, v in w["params"].items()})
+    o.set_state(w["q"])
+    t0 = time.perf_counter()
+    o.step(budget_steps)
+    dt = time.perf_counter() - t0
+    nc = len(w["cells"])
+    return {"value": nc * budget_steps / dt, "unit": "cell-updates/s", "cores": oracle.get_threads(),
+            "kind": "oracle", "sample": f"{budget_steps} S2O4 step(s) of the full {nc}-cell mesh, FP64, "
+                                        f"{oracle.get_threads()} OpenMP threads ({dt:.1f} s)"}
+
+
+def run_reference(args, rank, world):
+    """The CPU checker as it stands on the host cores (rank 0 only).  Each
+    timed step is one S2O4 step of a bounded sample of the workload: the
+    24^3 x 6 jittered mesh for the density-wave workloads."""
+    if rank != 0:
+        return
+    import oracle
+
+    w = workload(args.workload)
+    ws = workload("density24") if args.workload.startswith("density") else w
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    o = oracle.Oracle(ws["xyz"], ws["cells"], ws["periods"], ws.get("bfn"), ws.get("bft"),
+                      **{{"tau_num_c": "tau_c", "q_inf": "qinf"}.get(k, k): v for k, v in ws["params"].items()})
+    o.set_state(ws["q"])
+    o.step(min(args.warmup, 1))
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    nc = len(ws["cells"])
+    val = nc * args.steps / dt
+    line = {"impl": "reference", "metric": "cell-updates/s", "value": val, "unit": "cell-updates/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["desc"], "sample": f"{nc}-cell mesh per timed step"},
+            "cpu_baseline": {"value": val, "unit": "cell-updates/s", "cores": oracle.get_threads(), "kind": "oracle",
+                             "sample": f"{args.steps} S2O4 steps of the {nc}-cell mesh"},
+            "e2e": {"value": val, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="hgks", choices=["hgks", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--workload", default="density48")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    from paper_2407_00656_b300 import hgks as H
+
+    H.lib()
+    prec = H.HGKS_FP64 if args.precision == "fp64" else H.HGKS_FP32_MIXED
+    w = workload(args.workload)
+    nc = len(w["cells"])
+    stream = torch.cuda.Stream()
+    mesh = H.Mesh(w["xyz"], w["cells"], w["periods"], w.get("bfn"), w.get("bft"))
+    solver = H.Solver(mesh, w["q"], precision=prec, stream=stream.cuda_stream, **w["params"])
+    W, K = max(args.warmup, 3), args.steps
+    solver.step(W)
+    solver.sync()
+    launches_per_step = 7 + (2 if w.get("bfn") is not None else 0)
+
+    # ---- device-timed region: K steps, inputs resident in HBM (graph replay)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            solver.step(K)
+            e1.record(stream)
+        e1.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = nc * K * world / (ms * 1e-3)
+
+    # ---- per-kernel-group times (separate profiled pass of K steps, events
+    # around each group on the solver's stream)
+    prof = solver.profile(K)
+    flux_ms = prof[2] / 2.0  # two flux launches per step
+    nf = H.Mesh(w["xyz"], w["cells"], w["periods"], w.get("bfn"), w.get("bft")).n_faces
+    roof = {"bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS, "kernel": "k_flux (FP64)",
+            "peak_source": "derived: 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz (measured FMA chain: 1.125 TFLOP/s)",
+            "achieved": None, "frac": None, "traffic": None,
+            "kernel_ms_per_step": {"finalize": prof[0], "ghost+recon": prof[1], "flux": prof[2], "update": prof[3]}}
+    if FP64_FLOPS_PER_FACE_INVISCID and prec == H.HGKS_FP64 and not w["params"]:
+        ach = FP64_FLOPS_PER_FACE_INVISCID * nf / (flux_ms * 1e-3) / 1e12
+        roof["achieved"] = ach
+        roof["frac"] = ach / FP64_PEAK_TFLOPS
+
+    # ---- end to end through the C ABI with host buffers: per step the state
+    # goes host -> device, one step runs, the state comes back
+    qh = torch.from_numpy(np.ascontiguousarray(w["q"])).pin_memory().numpy()
+    out = torch.empty((nc, 5), dtype=torch.float64).pin_memory().numpy()
+    e2e_steps = max(2, min(K, 5))
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        solver.write(qh, 0.0)
+        solver.step(1)
+        solver.read(out)
+    t_e2e = time.perf_counter() - t0
+    e2e = {"value": nc * e2e_steps * world / t_e2e, "unit": "cell-updates/s",
+           "h2d_bytes_per_step": int(qh.nbytes), "d2h_bytes_per_step": int(out.nbytes)}
+
+    if rank == 0:
+        line = {"metric": "cell-updates/s", "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": K,
+                "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64" if prec == H.HGKS_FP64 else "f32-mixed", "data": "synthetic",
+                "config": {"workload": w["desc"], "cells": nc, "faces": nf, "precision": args.precision,
+                           "l2": "inputs larger than L2 (pseudo-inverses alone exceed 126 MB)",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roof, "e2e": e2e, "gpu_launches": K * launches_per_step + 1,
+                "clocks": clk.summary()}
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(w)
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

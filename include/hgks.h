@@ -1,0 +1,166 @@
+/*
+ * hgks.h -- C ABI of the HGKS hot-path library (libhgks.so) for one B300.
+ *
+ * The library advances the cell averages Q = (rho, rho U, rho V, rho W, rho E)
+ * of a 3D unstructured tetrahedral or hexahedral mesh with the high-order
+ * gas-kinetic scheme of arXiv 2407.00656:
+ *   - third-order non-compact WENO reconstruction over two-layer stencils
+ *     (Section 2.3, Eqs. polys and weno, Algorithm 1),
+ *   - the time-dependent BGK gas-kinetic flux at face Gauss points
+ *     (Section 2.1, Eqs. flux-G and flux; Section 2.2, Eq. expansion-1),
+ *   - the two-stage fourth-order (S2O4) update (Section 2.2),
+ *   - periodic, Riemann-invariant far-field and no-slip adiabatic wall
+ *     boundaries (Section 5.2).
+ *
+ * Conventions for every call below:
+ *   - Return 0 (HGKS_OK) or a negative HGKS_E* code; never abort.  The
+ *     message of the last failure on the calling thread is hgks_last_error().
+ *   - Host arrays passed in are read during the call only; the caller keeps
+ *     ownership.  Host output arrays are written by the call.
+ *   - Cell data at this boundary is always in the caller's cell order; the
+ *     library reorders cells internally along a space-filling curve.
+ *   - Floating point is IEEE binary64 unless stated otherwise.
+ */
+#ifndef HGKS_H
+#define HGKS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hgks_mesh hgks_mesh;     /* host-side mesh, built by hgks_mesh_create */
+typedef struct hgks_solver hgks_solver; /* device-resident solver state */
+
+enum {
+  HGKS_OK = 0,
+  HGKS_EINVAL = -1,     /* bad argument */
+  HGKS_ENOMEM = -2,     /* host or device allocation failed */
+  HGKS_EMESH = -3,      /* inconsistent mesh, degenerate cell or rank-deficient stencil */
+  HGKS_ECUDA = -4,      /* CUDA runtime error */
+  HGKS_ENONFINITE = -5, /* a non-finite cell average was produced */
+  HGKS_ETIMEOUT = -6    /* a bounded device wait ran out */
+};
+enum { HGKS_TET4 = 4, HGKS_HEX8 = 8 };
+enum { HGKS_BC_PERIODIC = 1, HGKS_BC_FARFIELD = 2, HGKS_BC_WALL = 3 };
+enum { HGKS_FP64 = 0, HGKS_FP32_MIXED = 1 };
+
+/* Mesh description (Section 3.1).  All cells have the same type.
+ *   xyz         [n_nodes][3] node coordinates.
+ *   cell_nodes  [n_cells][cell_type] node indices.  Tet: local face p is the
+ *               face opposite node p.  Hex: nodes 0-3 one quad, 4-7 the
+ *               opposite quad in the same order; local faces (0,1,2,3),
+ *               (0,1,5,4), (1,2,6,5), (2,3,7,6), (3,0,4,7), (4,5,6,7).
+ *   bface_nodes [n_bfaces][4] nodes of tagged boundary faces (-1 pads a
+ *               triangle), bface_tag[n_bfaces] one of HGKS_BC_*.
+ *   periods     [3] translation lengths along x, y, z used to pair untagged
+ *               boundary faces periodically (0 = not periodic), or NULL.
+ *   sfc_reorder 1: order cells along a Morton curve (recommended), 0: keep. */
+typedef struct {
+  int64_t n_nodes;
+  const double* xyz;
+  int64_t n_cells;
+  int32_t cell_type;
+  int32_t sfc_reorder;
+  const int64_t* cell_nodes;
+  int64_t n_bfaces;
+  const int64_t* bface_nodes;
+  const int32_t* bface_tag;
+  const double* periods;
+} hgks_mesh_desc;
+
+/* Physical and numerical parameters.
+ *   gamma          specific heat ratio; internal degrees of freedom
+ *                  K = (5 - 3 gamma)/(gamma - 1) (Section 2.1).
+ *   mu_ref, T_ref, visc_exp   viscosity mu = mu_ref (T/T_ref)^visc_exp with
+ *                  T = p/rho (Section 5.2); mu_ref = 0 gives the Euler flux.
+ *   Pr             Prandtl number (heat-flux correction of the BGK model).
+ *   cfl            time step: dt = cfl min_i h_i/(|U_i|+c_i), h_i =
+ *                  3|cell_i|/|surface_i|, and with viscosity also
+ *                  dt <= cfl min_i rho_i h_i^2/(2 mu_i).
+ *   tau_num_c      numerical collision time coefficient C in
+ *                  tau = mu/p + C dt |p_l - p_r|/(p_l + p_r).
+ *   weno_eps, weno_gamma_lin  WENO epsilon and sub-stencil linear weight
+ *                  (gamma_0 = 1 - M weno_gamma_lin), Section 2.3.
+ *   q_inf          conservative far-field free stream.
+ *   precision      HGKS_FP64, or HGKS_FP32_MIXED: reconstruction and flux
+ *                  in binary32, geometry, inverses and S2O4 in binary64.
+ *   use_graph      1: replay each step as one captured CUDA graph.
+ *   stream         cudaStream_t to run on, or NULL for a library stream. */
+typedef struct {
+  double gamma, mu_ref, T_ref, visc_exp, Pr, cfl, tau_num_c, weno_eps, weno_gamma_lin;
+  double q_inf[5];
+  int32_t precision;
+  int32_t use_graph;
+  void* stream;
+} hgks_params;
+
+/* Fill *p with defaults: gamma 1.4, inviscid, Pr 1, cfl 0.4, weno_eps 1e-8,
+ * weno_gamma_lin 0.025, q_inf = (1,0,0,0,2.5), FP64, graphs on, NULL stream. */
+void hgks_params_default(hgks_params* p);
+
+/* Build the host mesh: faces, periodic pairing, boundary ghosts, two-layer
+ * WENO stencils and sub-stencils, geometry, face Gauss points and the
+ * least-squares pseudo-inverses (Section 3.1, Algorithm 1; Section 2.3).
+ * Inputs are copied.  On success *out owns a new mesh.  Errors: HGKS_EINVAL
+ * (bad sizes/pointers), HGKS_EMESH (non-positive volume, unmatched boundary
+ * face, rank-deficient stencil), HGKS_ENOMEM. */
+int hgks_mesh_create(const hgks_mesh_desc* desc, hgks_mesh** out);
+
+/* Free a mesh that was never handed to hgks_init.  NULL is ignored. */
+void hgks_mesh_destroy(hgks_mesh* mesh);
+
+/* Mesh facts: what = 0 cells, 1 faces, 2 boundary ghosts, 3 padded big
+ * stencil size, 4 sub-stencil count, 5 device bytes hgks_init would allocate
+ * for precision 0, 6 the same for precision 1.  Returns -1 for bad input. */
+int64_t hgks_mesh_info(const hgks_mesh* mesh, int what);
+
+/* Create a solver: copy the mesh and the initial cell averages q0
+ * ([n_cells][5] host, caller order) to the device.  On HGKS_OK the solver owns
+ * the mesh (do not destroy it separately); on failure the caller still owns
+ * it.  Device memory is one cudaMalloc arena sized by hgks_mesh_info(.,5|6). */
+int hgks_init(hgks_mesh* mesh, const hgks_params* params, const double* q0, hgks_solver** out);
+
+/* Replace the state with q ([n_cells][5] host, caller order) at time t and
+ * reset the step counter (restart / resume). */
+int hgks_write(hgks_solver* s, const double* q, double t);
+
+/* Advance n_steps S2O4 steps asynchronously on the solver's stream (Algorithm
+ * 2: time step, then two stages of reconstruction, flux and update).
+ * dt_fixed > 0 uses that step; otherwise the CFL step above.  t_end > 0 clips
+ * the last step to land on t_end; steps after t_end do nothing.  No host
+ * synchronisation; device-side faults surface at hgks_read / hgks_sync. */
+int hgks_step(hgks_solver* s, int n_steps, double t_end, double dt_fixed);
+
+/* Wait for queued work; return HGKS_ENONFINITE if a step produced a
+ * non-finite average, HGKS_ECUDA on a runtime error. */
+int hgks_sync(hgks_solver* s);
+
+/* Synchronise and copy out the state ([n_cells][5] host, caller order), the
+ * time and the number of steps taken since init/write.  Any pointer may be
+ * NULL.  Returns the hgks_sync status. */
+int hgks_read(hgks_solver* s, double* q_out, double* t_out, int64_t* steps_out);
+
+/* One stage operator of the current state (Eq. finite with Section 2.2):
+ * L = dQ/dt and dL/dt ([n_cells][5] host each, caller order) for step dt.
+ * Test and diagnostic entry point; synchronises. */
+int hgks_stage_operator(hgks_solver* s, double dt, double* L_out, double* dL_out);
+
+/* Diagnostic: advance n_steps steps without graph replay, timing the kernel
+ * groups of each step with CUDA events on the solver's stream.  ms_out[4]
+ * receives the average milliseconds per step spent in: the time-step
+ * finalisation, ghost filling plus reconstruction (both stages), the face
+ * flux (both stages) and the two S2O4 updates.  Synchronises every step. */
+int hgks_profile(hgks_solver* s, int n_steps, double t_end, double dt_fixed, double* ms_out);
+
+/* Free the solver, its mesh and its device memory.  NULL is ignored. */
+void hgks_destroy(hgks_solver* s);
+
+/* Message of the last failure on this thread ("" if none). */
+const char* hgks_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HGKS_H */

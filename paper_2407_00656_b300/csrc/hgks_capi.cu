@@ -1,0 +1,420 @@
+// hgks_capi.cu -- the C ABI of libhgks: mesh creation, solver lifecycle,
+// stepping, state transfer and errors.  Every step of the scheme runs in the
+// kernels of hgks_kernels.cu; this file only moves data and orders launches.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hgks.h"
+#include "hgks_internal.h"
+#include "mesh_builder.h"
+
+struct hgks_mesh {
+  hgks::HostMesh m;
+};
+
+struct hgks_solver {
+  hgks::HostMesh mesh;
+  hgks::DevMesh dm{};
+  hgks::DevParams dp{};
+  hgks::DevWork dw{};
+  int precision = 0;
+  int use_graph = 1;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  cudaGraphExec_t graph = nullptr;
+  std::vector<double> hbuf;  // host staging in the internal SoA layout
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return HGKS_ECUDA;
+}
+
+#define HGKS_CUDA(call, what)                   \
+  do {                                          \
+    cudaError_t e_ = (call);                    \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+// Bump allocator over the solver's single device arena.
+struct Carver {
+  char* base;
+  size_t off = 0, cap;
+  template <typename T>
+  T* take(int64_t n) {
+    off = (off + 255) / 256 * 256;
+    T* p = reinterpret_cast<T*>(base + off);
+    off += sizeof(T) * (size_t)n;
+    return p;
+  }
+};
+
+template <typename T>
+cudaError_t up(T* dst, const std::vector<T>& src) {
+  return cudaMemcpy(dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
+}
+
+int check_params(const hgks_params* p) {
+  if (!p) return fail(HGKS_EINVAL, "params is NULL");
+  if (!(p->gamma > 1.0 && p->gamma < 5.0 / 3.0 + 1e-12)) return fail(HGKS_EINVAL, "gamma must lie in (1, 5/3]");
+  if (!(p->cfl > 0.0)) return fail(HGKS_EINVAL, "cfl must be positive");
+  if (!(p->mu_ref >= 0.0) || !(p->tau_num_c >= 0.0)) return fail(HGKS_EINVAL, "mu_ref and tau_num_c must be >= 0");
+  if (p->mu_ref > 0.0 && p->visc_exp != 0.0 && !(p->T_ref > 0.0)) return fail(HGKS_EINVAL, "T_ref must be positive");
+  if (!(p->Pr > 0.0)) return fail(HGKS_EINVAL, "Pr must be positive");
+  if (!(p->weno_eps > 0.0)) return fail(HGKS_EINVAL, "weno_eps must be positive");
+  if (!(p->weno_gamma_lin > 0.0 && p->weno_gamma_lin < 0.125)) return fail(HGKS_EINVAL, "weno_gamma_lin must lie in (0, 1/8)");
+  if (p->precision != HGKS_FP64 && p->precision != HGKS_FP32_MIXED) return fail(HGKS_EINVAL, "unknown precision");
+  return HGKS_OK;
+}
+
+// caller order [n][5] -> internal SoA [5][stride] (new order)
+void to_internal(const hgks::HostMesh& m, const double* q, std::vector<double>& h, int64_t stride) {
+  h.assign(5 * stride, 0.0);
+  for (int64_t c = 0; c < m.nc; ++c) {
+    const double* s = q + 5 * m.perm[c];
+    for (int v = 0; v < 5; ++v) h[v * stride + c] = s[v];
+  }
+}
+void to_caller(const hgks::HostMesh& m, const double* h, int64_t stride, double* q) {
+  for (int64_t c = 0; c < m.nc; ++c) {
+    double* d = q + 5 * m.perm[c];
+    for (int v = 0; v < 5; ++v) d[v] = h[v * stride + c];
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+void hgks_params_default(hgks_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->gamma = 1.4;
+  p->mu_ref = 0.0;
+  p->T_ref = 1.0;
+  p->visc_exp = 0.0;
+  p->Pr = 1.0;
+  p->cfl = 0.4;
+  p->tau_num_c = 0.0;
+  p->weno_eps = 1e-8;
+  p->weno_gamma_lin = 0.025;
+  p->q_inf[0] = 1.0;
+  p->q_inf[4] = 2.5;
+  p->precision = HGKS_FP64;
+  p->use_graph = 1;
+  p->stream = nullptr;
+}
+
+const char* hgks_last_error(void) { return g_err.c_str(); }
+
+int hgks_mesh_create(const hgks_mesh_desc* d, hgks_mesh** out) {
+  if (!d || !out) return fail(HGKS_EINVAL, "NULL argument");
+  *out = nullptr;
+  if (d->cell_type != HGKS_TET4 && d->cell_type != HGKS_HEX8) return fail(HGKS_EINVAL, "cell_type must be 4 or 8");
+  if (d->n_nodes <= 0 || d->n_cells <= 0 || !d->xyz || !d->cell_nodes)
+    return fail(HGKS_EINVAL, "empty mesh or NULL node/cell arrays");
+  if (d->n_bfaces < 0 || (d->n_bfaces > 0 && (!d->bface_nodes || !d->bface_tag)))
+    return fail(HGKS_EINVAL, "bad boundary face arrays");
+  try {
+    hgks_mesh* mesh = new hgks_mesh;
+    std::string err;
+    int rc = hgks::build_host_mesh(*d, mesh->m, err);
+    if (rc == HGKS_OK && !hgks::stencil_supported(mesh->m.nfc, mesh->m.K)) {
+      rc = HGKS_EMESH;
+      err = "stencil size " + std::to_string(mesh->m.K) + " is not among the compiled shapes";
+    }
+    if (rc != HGKS_OK) {
+      delete mesh;
+      return fail(rc, err);
+    }
+    *out = mesh;
+    return HGKS_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(HGKS_ENOMEM, "host allocation failed while building the mesh");
+  }
+}
+
+void hgks_mesh_destroy(hgks_mesh* mesh) { delete mesh; }
+
+int64_t hgks_mesh_info(const hgks_mesh* mesh, int what) {
+  if (!mesh) return -1;
+  const hgks::HostMesh& m = mesh->m;
+  switch (what) {
+    case 0: return m.nc;
+    case 1: return m.nf;
+    case 2: return m.ng;
+    case 3: return m.K;
+    case 4: return m.M;
+    case 5: return hgks::device_bytes(m, HGKS_FP64);
+    case 6: return hgks::device_bytes(m, HGKS_FP32_MIXED);
+    default: return -1;
+  }
+}
+
+int hgks_init(hgks_mesh* mesh, const hgks_params* params, const double* q0, hgks_solver** out) {
+  if (!mesh || !out || !q0) return fail(HGKS_EINVAL, "NULL argument");
+  *out = nullptr;
+  int rc = check_params(params);
+  if (rc) return rc;
+  hgks_solver* s = nullptr;
+  try {
+    s = new hgks_solver;
+  } catch (const std::bad_alloc&) {
+    return fail(HGKS_ENOMEM, "host allocation failed");
+  }
+  auto bail = [&](int code) {
+    if (s->arena) cudaFree(s->arena);
+    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+    // hand the mesh back to the caller untouched
+    std::swap(mesh->m, s->mesh);
+    delete s;
+    return code;
+  };
+  std::swap(s->mesh, mesh->m);
+  const hgks::HostMesh& m = s->mesh;
+  s->precision = params->precision;
+  s->use_graph = params->use_graph;
+  const size_t bytes = (size_t)hgks::device_bytes(m, s->precision);
+  cudaError_t e = cudaMalloc(&s->arena, bytes);
+  if (e != cudaSuccess) {
+    s->arena = nullptr;
+    cudaGetLastError();
+    char b[160];
+    std::snprintf(b, sizeof b, "device allocation of %.3f GB failed: %s", bytes / 1e9, cudaGetErrorString(e));
+    g_err = b;
+    return bail(HGKS_ENOMEM);
+  }
+  s->arena_bytes = bytes;
+  if (params->stream) {
+    s->stream = static_cast<cudaStream_t>(params->stream);
+  } else {
+    e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { cuda_fail(e, "cudaStreamCreate"); return bail(HGKS_ECUDA); }
+    s->own_stream = true;
+  }
+  // carve the arena
+  Carver cv{static_cast<char*>(s->arena), 0, bytes};
+  hgks::DevMesh& dm = s->dm;
+  dm.nc = m.nc; dm.nf = m.nf; dm.ng = m.ng; dm.nce = m.nc + m.ng;
+  dm.K = m.K; dm.M = m.M; dm.KM = m.KM; dm.G = m.G; dm.nfc = m.nfc;
+  std::vector<double> volinv(m.nc);
+  for (int64_t c = 0; c < m.nc; ++c) volinv[c] = 1.0 / m.vol[c];
+  double* p_volinv = cv.take<double>(m.nc);
+  double* p_hdt = cv.take<double>(m.nc);
+  double* p_hinv = cv.take<double>(m.nc);
+  cv.take<double>(m.nc);  // spare slot kept by the size formula
+  cv.take<double>(3 * m.nc);  // centroids are baked into the face offsets; slot kept for the size formula
+  double* p_mom = cv.take<double>(6 * m.nc);
+  int32_t* p_sten = cv.take<int32_t>((int64_t)m.K * m.nc);
+  double* p_pinv0 = cv.take<double>((int64_t)9 * m.K * m.nc);
+  uint8_t* p_subidx = cv.take<uint8_t>((int64_t)m.M * m.KM * m.nc);
+  double* p_pinvm = cv.take<double>((int64_t)m.M * 3 * m.KM * m.nc);
+  int32_t* p_cface = cv.take<int32_t>((int64_t)m.nfc * m.nc);
+  int32_t* p_gsrc = cv.take<int32_t>(m.ng);
+  int32_t* p_gtag = cv.take<int32_t>(m.ng);
+  double* p_gnrm = cv.take<double>(3 * m.ng);
+  int32_t* p_fown = cv.take<int32_t>(m.nf);
+  int32_t* p_fnbr = cv.take<int32_t>(m.nf);
+  double* p_fdl = cv.take<double>((int64_t)m.G * 3 * m.nf);
+  double* p_fdr = cv.take<double>((int64_t)m.G * 3 * m.nf);
+  double* p_fn = cv.take<double>((int64_t)m.G * 3 * m.nf);
+  double* p_fw = cv.take<double>((int64_t)m.G * m.nf);
+  hgks::DevWork& w = s->dw;
+  w.Q = cv.take<double>(5 * dm.nce);
+  w.Qs = cv.take<double>(5 * dm.nce);
+  w.R = cv.take<double>(5 * m.nc);
+  w.Qf = s->precision == HGKS_FP32_MIXED ? cv.take<float>(5 * dm.nce) : nullptr;
+  const int64_t rs = s->precision == HGKS_FP32_MIXED ? 4 : 8;
+  w.coef = cv.take<char>(rs * 50 * m.nc);
+  w.Fs = cv.take<char>(rs * 10 * m.nf);
+  w.ctl = cv.take<hgks::Control>(1);
+  if (cv.off > bytes) { g_err = "internal error: arena too small"; return bail(HGKS_ENOMEM); }
+  dm.volinv = p_volinv; dm.hdt = p_hdt; dm.hinv = p_hinv; dm.mom = p_mom; dm.sten = p_sten; dm.pinv0 = p_pinv0;
+  dm.subidx = p_subidx; dm.pinvm = p_pinvm; dm.cface = p_cface; dm.gsrc = p_gsrc; dm.gtag = p_gtag; dm.gnrm = p_gnrm;
+  dm.fown = p_fown; dm.fnbr = p_fnbr; dm.fdl = p_fdl; dm.fdr = p_fdr; dm.fn = p_fn; dm.fw = p_fw;
+  cudaError_t ue = cudaSuccess;
+  auto chk = [&](cudaError_t x) { if (ue == cudaSuccess) ue = x; };
+  chk(up(p_volinv, volinv));
+  chk(up(p_hdt, m.hdt));
+  chk(up(p_hinv, m.hinv));
+  chk(up(p_mom, m.mom));
+  chk(up(p_sten, m.sten));
+  chk(up(p_pinv0, m.pinv0));
+  chk(up(p_subidx, m.subidx));
+  chk(up(p_pinvm, m.pinvm));
+  chk(up(p_cface, m.cface));
+  if (m.ng) {
+    chk(up(p_gsrc, m.gsrc));
+    chk(up(p_gtag, m.gtag));
+    chk(up(p_gnrm, m.gnrm));
+  }
+  chk(up(p_fown, m.fown));
+  chk(up(p_fnbr, m.fnbr));
+  chk(up(p_fdl, m.fdl));
+  chk(up(p_fdr, m.fdr));
+  chk(up(p_fn, m.fn));
+  chk(up(p_fw, m.fw));
+  chk(cudaMemset(w.Q, 0, sizeof(double) * 5 * dm.nce));
+  chk(cudaMemset(w.Qs, 0, sizeof(double) * 5 * dm.nce));
+  if (ue != cudaSuccess) { cuda_fail(ue, "uploading the mesh"); return bail(HGKS_ECUDA); }
+  // parameters
+  hgks::DevParams& dp = s->dp;
+  dp.gamma = params->gamma;
+  dp.Kint = (5.0 - 3.0 * params->gamma) / (params->gamma - 1.0);
+  dp.mu_ref = params->mu_ref;
+  dp.T_ref = params->T_ref;
+  dp.visc_exp = params->visc_exp;
+  dp.Pr = params->Pr;
+  dp.cfl = params->cfl;
+  dp.tau_c = params->tau_num_c;
+  dp.eps = params->weno_eps;
+  dp.glin = params->weno_gamma_lin;
+  for (int i = 0; i < 5; ++i) dp.qinf[i] = params->q_inf[i];
+  dp.viscous = (params->mu_ref > 0.0 || params->tau_num_c > 0.0) ? 1 : 0;
+  hgks::prepare_kernels(dm, s->precision);
+  // initial state
+  to_internal(m, q0, s->hbuf, dm.nce);
+  e = cudaMemcpyAsync(w.Q, s->hbuf.data(), sizeof(double) * 5 * dm.nce, cudaMemcpyHostToDevice, s->stream);
+  if (e != cudaSuccess) { cuda_fail(e, "copying the initial state"); return bail(HGKS_ECUDA); }
+  hgks::launch_reset(dm, dp, w, s->precision, 0.0, s->stream);
+  e = cudaStreamSynchronize(s->stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) { cuda_fail(e, "initialising the solver"); return bail(HGKS_ECUDA); }
+  // the solver now owns the mesh: leave the caller's handle empty and free it
+  delete mesh;
+  *out = s;
+  return HGKS_OK;
+}
+
+int hgks_write(hgks_solver* s, const double* q, double t) {
+  if (!s || !q) return fail(HGKS_EINVAL, "NULL argument");
+  to_internal(s->mesh, q, s->hbuf, s->dm.nce);
+  HGKS_CUDA(cudaStreamSynchronize(s->stream), "waiting for queued work");
+  HGKS_CUDA(cudaMemcpyAsync(s->dw.Q, s->hbuf.data(), sizeof(double) * 5 * s->dm.nce, cudaMemcpyHostToDevice, s->stream),
+            "copying the state");
+  hgks::launch_reset(s->dm, s->dp, s->dw, s->precision, t, s->stream);
+  HGKS_CUDA(cudaStreamSynchronize(s->stream), "writing the state");
+  HGKS_CUDA(cudaGetLastError(), "writing the state");
+  return HGKS_OK;
+}
+
+int hgks_step(hgks_solver* s, int n_steps, double t_end, double dt_fixed) {
+  if (!s) return fail(HGKS_EINVAL, "NULL solver");
+  if (n_steps < 0) return fail(HGKS_EINVAL, "n_steps must be >= 0");
+  if (n_steps == 0) return HGKS_OK;
+  hgks::launch_control(s->dw, t_end, dt_fixed, s->stream);
+  if (s->use_graph) {
+    if (!s->graph) {
+      cudaGraph_t g = nullptr;
+      HGKS_CUDA(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal), "beginning graph capture");
+      hgks::launch_step(s->dm, s->dp, s->dw, s->precision, s->stream);
+      cudaError_t e = cudaStreamEndCapture(s->stream, &g);
+      if (e != cudaSuccess) return cuda_fail(e, "capturing the step graph");
+      e = cudaGraphInstantiate(&s->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        s->graph = nullptr;
+        return cuda_fail(e, "instantiating the step graph");
+      }
+    }
+    for (int i = 0; i < n_steps; ++i) HGKS_CUDA(cudaGraphLaunch(s->graph, s->stream), "launching the step graph");
+  } else {
+    for (int i = 0; i < n_steps; ++i) hgks::launch_step(s->dm, s->dp, s->dw, s->precision, s->stream);
+  }
+  HGKS_CUDA(cudaGetLastError(), "launching the step");
+  return HGKS_OK;
+}
+
+int hgks_sync(hgks_solver* s) {
+  if (!s) return fail(HGKS_EINVAL, "NULL solver");
+  HGKS_CUDA(cudaStreamSynchronize(s->stream), "synchronising");
+  HGKS_CUDA(cudaGetLastError(), "synchronising");
+  hgks::Control c;
+  HGKS_CUDA(cudaMemcpy(&c, s->dw.ctl, sizeof c, cudaMemcpyDeviceToHost), "reading the control block");
+  if (c.flags & hgks::FLAG_NONFINITE) return fail(HGKS_ENONFINITE, "a step produced a non-finite cell average");
+  return HGKS_OK;
+}
+
+int hgks_read(hgks_solver* s, double* q_out, double* t_out, int64_t* steps_out) {
+  if (!s) return fail(HGKS_EINVAL, "NULL solver");
+  HGKS_CUDA(cudaStreamSynchronize(s->stream), "synchronising");
+  hgks::Control c;
+  HGKS_CUDA(cudaMemcpy(&c, s->dw.ctl, sizeof c, cudaMemcpyDeviceToHost), "reading the control block");
+  if (q_out) {
+    s->hbuf.resize(5 * s->dm.nce);
+    HGKS_CUDA(cudaMemcpy(s->hbuf.data(), s->dw.Q, sizeof(double) * 5 * s->dm.nce, cudaMemcpyDeviceToHost),
+              "reading the state");
+    to_caller(s->mesh, s->hbuf.data(), s->dm.nce, q_out);
+  }
+  if (t_out) *t_out = c.t;
+  if (steps_out) *steps_out = c.steps;
+  if (c.flags & hgks::FLAG_NONFINITE) return fail(HGKS_ENONFINITE, "a step produced a non-finite cell average");
+  return HGKS_OK;
+}
+
+int hgks_stage_operator(hgks_solver* s, double dt, double* L_out, double* dL_out) {
+  if (!s || !L_out || !dL_out) return fail(HGKS_EINVAL, "NULL argument");
+  if (!(dt > 0.0)) return fail(HGKS_EINVAL, "dt must be positive");
+  const int64_t nc = s->dm.nc;
+  // the stage buffers Q* and R are free between steps
+  hgks::launch_operator(s->dm, s->dp, s->dw, s->precision, dt, s->dw.Qs, s->dw.R, s->stream);
+  HGKS_CUDA(cudaStreamSynchronize(s->stream), "evaluating the stage operator");
+  HGKS_CUDA(cudaGetLastError(), "evaluating the stage operator");
+  std::vector<double> h(5 * nc);
+  HGKS_CUDA(cudaMemcpy(h.data(), s->dw.Qs, sizeof(double) * 5 * nc, cudaMemcpyDeviceToHost), "reading L");
+  to_caller(s->mesh, h.data(), nc, L_out);
+  HGKS_CUDA(cudaMemcpy(h.data(), s->dw.R, sizeof(double) * 5 * nc, cudaMemcpyDeviceToHost), "reading dL/dt");
+  to_caller(s->mesh, h.data(), nc, dL_out);
+  return HGKS_OK;
+}
+
+int hgks_profile(hgks_solver* s, int n_steps, double t_end, double dt_fixed, double* ms_out) {
+  if (!s || !ms_out || n_steps <= 0) return fail(HGKS_EINVAL, "bad argument");
+  hgks::StepEvents ev;
+  for (int i = 0; i < 8; ++i) HGKS_CUDA(cudaEventCreate(&ev.ev[i]), "creating events");
+  double acc[4] = {0, 0, 0, 0};
+  hgks::launch_control(s->dw, t_end, dt_fixed, s->stream);
+  int rc = HGKS_OK;
+  for (int k = 0; k < n_steps && rc == HGKS_OK; ++k) {
+    hgks::launch_step(s->dm, s->dp, s->dw, s->precision, s->stream, &ev);
+    cudaError_t e = cudaEventSynchronize(ev.ev[7]);
+    if (e != cudaSuccess) { rc = cuda_fail(e, "profiling a step"); break; }
+    float t[7];
+    for (int i = 0; i < 7; ++i) cudaEventElapsedTime(&t[i], ev.ev[i], ev.ev[i + 1]);
+    acc[0] += t[0];
+    acc[1] += t[1] + t[4];
+    acc[2] += t[2] + t[5];
+    acc[3] += t[3] + t[6];
+  }
+  for (int i = 0; i < 8; ++i) cudaEventDestroy(ev.ev[i]);
+  for (int i = 0; i < 4; ++i) ms_out[i] = acc[i] / n_steps;
+  return rc;
+}
+
+void hgks_destroy(hgks_solver* s) {
+  if (!s) return;
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  if (s->graph) cudaGraphExecDestroy(s->graph);
+  if (s->arena) cudaFree(s->arena);
+  if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+  delete s;
+}
+
+}  // extern "C"

@@ -1,0 +1,90 @@
+// hgks_internal.h -- device-side data layout shared by the kernels and the
+// solver lifecycle code of libhgks.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace hgks {
+
+// Read-only mesh arrays in device memory (layouts as in mesh_builder.h).
+struct DevMesh {
+  int64_t nc, nf, ng, nce;  // cells, faces, ghosts, cells + ghosts
+  int K, M, KM, G, nfc;
+  const double* volinv;   // [nc] 1/|cell|
+  const double* hdt;      // [nc]
+  const double* hinv;     // [nc]
+  const double* mom;      // [6][nc] scaled central second moments
+  const int32_t* sten;    // [K][nc]
+  const double* pinv0;    // [9K][nc]
+  const uint8_t* subidx;  // [M*KM][nc]
+  const double* pinvm;    // [M*3*KM][nc]
+  const int32_t* cface;   // [nfc][nc]
+  const int32_t* gsrc;    // [ng]
+  const int32_t* gtag;    // [ng]
+  const double* gnrm;     // [3][ng]
+  const int32_t* fown;    // [nf]
+  const int32_t* fnbr;    // [nf]
+  const double* fdl;      // [3G][nf]
+  const double* fdr;      // [3G][nf]
+  const double* fn;       // [3G][nf]
+  const double* fw;       // [G][nf]
+};
+
+// Physical and numerical parameters as the kernels use them.
+struct DevParams {
+  double gamma, Kint, mu_ref, T_ref, visc_exp, Pr, cfl, tau_c, eps, glin;
+  double qinf[5];
+  int viscous;  // 1 when mu_ref > 0 or tau_c > 0 (collision time may be non-zero)
+};
+
+// Step control block in device memory.
+struct Control {
+  double t;          // time reached by the queued steps
+  double dt;         // step size of the step in flight (0: no-op step)
+  double t_end;      // > 0: clip steps to land on t_end
+  double dt_fixed;   // > 0: use instead of the CFL step
+  unsigned long long dtmin_bits;  // min over cells of the local step bound (bits of a positive double)
+  long long steps;   // steps taken since init/write
+  int flags;         // bit 0: a non-finite cell average was produced
+  int pad;
+};
+
+enum { FLAG_NONFINITE = 1 };
+
+// Work arrays of one solver.
+struct DevWork {
+  double* Q;      // [5][nce] state Q^n, ghost slots at [nc, nce)
+  double* Qs;     // [5][nce] stage state Q*
+  double* R;      // [5][nc]  Q^n + dt L^n + dt^2/6 dL^n
+  float* Qf;      // [5][nce] binary32 copy of the stage state (mixed precision only)
+  void* coef;     // [50][nc] reconstruction polynomials (double or float)
+  void* Fs;       // [10][nf] face flux sums: F (5) then dF/dt (5) (double or float)
+  Control* ctl;
+};
+
+// Per-instantiation kernel attributes; call once per solver before capture.
+void prepare_kernels(const DevMesh& m, int precision);
+// True if the kernels are compiled for this stencil shape (faces per cell, K).
+bool stencil_supported(int nfc, int K);
+// Optional events recorded between the kernel groups of one step:
+// ev[0] | finalize | ev[1] | ghost+recon | ev[2] | flux | ev[3] | update1 | ev[4]
+//       | ghost+recon | ev[5] | flux | ev[6] | update2 | ev[7]
+struct StepEvents {
+  cudaEvent_t ev[8];
+};
+
+// Launch one S2O4 step (Algorithm 2) on stream s; precision 0 = FP64, 1 = mixed.
+void launch_step(const DevMesh& m, const DevParams& p, const DevWork& w, int precision, cudaStream_t s,
+                 const StepEvents* ev = nullptr);
+// Set t_end and dt_fixed for the following steps.
+void launch_control(const DevWork& w, double t_end, double dt_fixed, cudaStream_t s);
+// Reset time/steps/flags, copy the binary32 state if needed and compute the
+// first step bound of the current state.
+void launch_reset(const DevMesh& m, const DevParams& p, const DevWork& w, int precision, double t, cudaStream_t s);
+// L and dL/dt of the current state for step dt into Qs[0:5] and R (as L) -- test path.
+void launch_operator(const DevMesh& m, const DevParams& p, const DevWork& w, int precision, double dt,
+                     double* L, double* dL, cudaStream_t s);
+
+}  // namespace hgks

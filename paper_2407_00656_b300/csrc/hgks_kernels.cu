@@ -1,0 +1,970 @@
+// hgks_kernels.cu -- sm_103a kernels of one HGKS step (Algorithm 2):
+//
+//   k_finalize    time step from the device-side minimum bound (Algorithm 2,
+//                 "calculate time step"), clipped to t_end
+//   k_ghost       boundary ghost cell averages (Algorithm 1 ghost cells)
+//   k_recon       third-order WENO reconstruction (Section 2.3, Eqs. polys,
+//                 weno), emitting one combined quadratic per cell and variable
+//   k_flux        time-dependent gas-kinetic flux at the face Gauss points
+//                 (Section 2.1, Eq. flux; Section 2.2 linear-in-time fit)
+//   k_update1/2   gather of the face fluxes per cell (no atomics) and the two
+//                 S2O4 stages (Section 2.2); stage 2 also produces the next
+//                 step bound and the non-finite flag
+//
+// Precision: Real = double (FP64) or float (FP32-mixed: reconstruction and
+// flux in binary32; geometry, pseudo-inverses and S2O4 sums in binary64).
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <cstdint>
+#include <type_traits>
+
+#include "hgks_internal.h"
+
+namespace hgks {
+namespace {
+
+constexpr int kBlock = 128;
+
+template <int N, int I = 0, class F>
+__device__ __forceinline__ void sfor(F&& f) {
+  if constexpr (I < N) {
+    f(std::integral_constant<int, I>{});
+    sfor<N, I + 1>(f);
+  }
+}
+
+// --------------------------------------------------------------------------
+// Maxwellian moments.  Mom holds normalised one-dimensional moments <u^k>,
+// <v^k>, <w^k> and <(xi^2)^k> of one Maxwellian (u possibly on a half-line).
+// --------------------------------------------------------------------------
+template <typename R>
+struct Mom {
+  R u[7], v[6], w[6], x[3];
+};
+
+template <int a, int b, int c, int d, typename R>
+__device__ __forceinline__ R mm(const Mom<R>& M) {
+  return M.u[a] * M.v[b] * M.w[c] * M.x[d];
+}
+// <u^a v^b w^c (xi^2)^d psi_i>, psi = (1, u, v, w, (u^2+v^2+w^2+xi^2)/2)
+template <int i, int a, int b, int c, int d, typename R>
+__device__ __forceinline__ R mpsi(const Mom<R>& M) {
+  if constexpr (i == 0) return mm<a, b, c, d>(M);
+  else if constexpr (i == 1) return mm<a + 1, b, c, d>(M);
+  else if constexpr (i == 2) return mm<a, b + 1, c, d>(M);
+  else if constexpr (i == 3) return mm<a, b, c + 1, d>(M);
+  else return R(0.5) * (mm<a + 2, b, c, d>(M) + mm<a, b + 2, c, d>(M) + mm<a, b, c + 2, d>(M) + mm<a, b, c, d + 1>(M));
+}
+// <u^a v^b w^c psi_i psi_j>
+template <int i, int j, int a, int b, int c, typename R>
+__device__ __forceinline__ R mpsi2(const Mom<R>& M) {
+  if constexpr (j == 0) return mpsi<i, a, b, c, 0>(M);
+  else if constexpr (j == 1) return mpsi<i, a + 1, b, c, 0>(M);
+  else if constexpr (j == 2) return mpsi<i, a, b + 1, c, 0>(M);
+  else if constexpr (j == 3) return mpsi<i, a, b, c + 1, 0>(M);
+  else
+    return R(0.5) * (mpsi<i, a + 2, b, c, 0>(M) + mpsi<i, a, b + 2, c, 0>(M) + mpsi<i, a, b, c + 2, 0>(M) +
+                     mpsi<i, a, b, c, 1>(M));
+}
+
+// Gaussian recursion <u^{n+2}> = U <u^{n+1}> + (n+1)/(2 lam) <u^n>
+template <int N, typename R>
+__device__ __forceinline__ void recur(R* m, R U, R h2) {
+#pragma unroll
+  for (int n = 0; n + 2 < N; ++n) m[n + 2] = U * m[n + 1] + R(n + 1) * h2 * m[n];
+}
+
+template <typename R>
+struct Prim {
+  R rho, U, V, W, lam, h2;  // h2 = 1/(2 lam)
+};
+
+template <typename R>
+__device__ __forceinline__ Prim<R> prim_of(const R q[5], R Kint) {
+  Prim<R> p;
+  p.rho = q[0];
+  const R ri = R(1) / q[0];
+  p.U = q[1] * ri;
+  p.V = q[2] * ri;
+  p.W = q[3] * ri;
+  // rho E = rho |U|^2 / 2 + (K+3) rho / (4 lam)
+  const R eint = q[4] - R(0.5) * (q[1] * p.U + q[2] * p.V + q[3] * p.W);
+  p.h2 = R(2) * eint / ((Kint + R(3)) * q[0]);
+  p.lam = R(0.5) / p.h2;
+  return p;
+}
+
+// Moments of a Maxwellian; half = +1: u > 0, -1: u < 0, 0: full line.
+template <int NU, typename R>
+__device__ __forceinline__ void moments(const Prim<R>& p, int half, R Kint, Mom<R>& M) {
+  if (half == 0) {
+    M.u[0] = R(1);
+    M.u[1] = p.U;
+  } else {
+    const R sl = sqrt(p.lam);
+    const R s = R(half) * sl * p.U;
+    const R e = exp(-p.lam * p.U * p.U) * R(0.28209479177387814) / sl;  // exp(-lam U^2)/(2 sqrt(pi lam))
+    M.u[0] = R(0.5) * erfc(-s);
+    M.u[1] = p.U * M.u[0] + R(half) * e;
+  }
+  recur<NU>(M.u, p.U, p.h2);
+  M.v[0] = R(1);
+  M.v[1] = p.V;
+  recur<6>(M.v, p.V, p.h2);
+  M.w[0] = R(1);
+  M.w[1] = p.W;
+  recur<6>(M.w, p.W, p.h2);
+  M.x[0] = R(1);
+  M.x[1] = Kint * p.h2;                        // <xi^2> = K/(2 lam)
+  M.x[2] = Kint * (Kint + R(2)) * p.h2 * p.h2;  // <xi^4> = K(K+2)/(4 lam^2)
+}
+
+// Micro-slope from a derivative dq of the conservative variables (Section
+// 2.1), in closed form: returns rho * a for the polynomial a(psi) with
+// rho <a psi> = dq under the Maxwellian p.
+template <typename R>
+__device__ __forceinline__ void micro_slope_rho(const Prim<R>& p, R Kint, const R dq[5], R a[5]) {
+  const R b0 = dq[0];
+  const R r1 = dq[1] - p.U * b0, r2 = dq[2] - p.V * b0, r3 = dq[3] - p.W * b0;
+  const R E = p.U * p.U + p.V * p.V + p.W * p.W + (Kint + R(3)) * p.h2;
+  const R r4 = R(2) * dq[4] - E * b0;
+  a[4] = R(4) * p.lam * p.lam / (Kint + R(3)) * (r4 - R(2) * (p.U * r1 + p.V * r2 + p.W * r3));
+  const R tl = R(2) * p.lam;
+  a[1] = tl * r1 - p.U * a[4];
+  a[2] = tl * r2 - p.V * a[4];
+  a[3] = tl * r3 - p.W * a[4];
+  a[0] = b0 - p.U * a[1] - p.V * a[2] - p.W * a[3] - R(0.5) * a[4] * E;
+}
+
+// Euler state used for flux Jacobians in the local frame.
+template <typename R>
+struct EState {
+  R rho, ri, u[3], m[3], E, p, gm1;
+};
+template <typename R>
+__device__ __forceinline__ EState<R> estate(const R q[5], R gamma) {
+  EState<R> s;
+  s.rho = q[0];
+  s.ri = R(1) / q[0];
+  for (int a = 0; a < 3; ++a) { s.m[a] = q[1 + a]; s.u[a] = q[1 + a] * s.ri; }
+  s.E = q[4];
+  s.gm1 = gamma - R(1);
+  s.p = s.gm1 * (q[4] - R(0.5) * (s.m[0] * s.u[0] + s.m[1] * s.u[1] + s.m[2] * s.u[2]));
+  return s;
+}
+// o = J_j(q) d: derivative of the Euler flux along axis j in direction d.
+// For a Maxwellian g(Q), rho <u_j psi a(dQ)> equals J_j dQ exactly, which
+// replaces the moment sums of the micro-slope terms.
+template <int j, typename R>
+__device__ __forceinline__ void euler_jv(const EState<R>& s, const R d[5], R o[5]) {
+  const R duj = (d[1 + j] - s.u[j] * d[0]) * s.ri;
+  const R dp = s.gm1 * (d[4] - (s.u[0] * d[1] + s.u[1] * d[2] + s.u[2] * d[3]) +
+                        R(0.5) * (s.u[0] * s.u[0] + s.u[1] * s.u[1] + s.u[2] * s.u[2]) * d[0]);
+  o[0] = d[1 + j];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) o[1 + a] = d[1 + a] * s.u[j] + s.m[a] * duj + (a == j ? dp : R(0));
+  o[4] = (d[4] + dp) * s.u[j] + (s.E + s.p) * duj;
+}
+
+template <typename R>
+struct FluxParams {
+  R gamma, Kint, mu_ref, T_ref, visc_exp, Pr, tau_c;
+};
+
+// <u psi_i P> for P = a.u (a_j micro-slopes along x, y, z, rho-weighted),
+// expanded into the twelve monomials of P.
+template <typename R>
+__device__ __forceinline__ void flux_of_slope(const Mom<R>& M, const R a[3][5], R X[5]) {
+  // P = sum_j u_j (a_j0 + a_j1 u + a_j2 v + a_j3 w + a_j4 psi4)
+  const R pu = a[0][0], pv = a[1][0], pw = a[2][0];
+  const R puu = a[0][1], puv = a[0][2] + a[1][1], puw = a[0][3] + a[2][1];
+  const R pvv = a[1][2], pvw = a[1][3] + a[2][2], pww = a[2][3];
+  const R pu4 = a[0][4], pv4 = a[1][4], pw4 = a[2][4];
+  sfor<5>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    X[i] = pu * mpsi<i, 2, 0, 0, 0>(M) + pv * mpsi<i, 1, 1, 0, 0>(M) + pw * mpsi<i, 1, 0, 1, 0>(M) +
+           puu * mpsi<i, 3, 0, 0, 0>(M) + puv * mpsi<i, 2, 1, 0, 0>(M) + puw * mpsi<i, 2, 0, 1, 0>(M) +
+           pvv * mpsi<i, 1, 2, 0, 0>(M) + pvw * mpsi<i, 1, 1, 1, 0>(M) + pww * mpsi<i, 1, 0, 2, 0>(M) +
+           pu4 * mpsi2<i, 4, 2, 0, 0>(M) + pv4 * mpsi2<i, 4, 1, 1, 0>(M) + pw4 * mpsi2<i, 4, 1, 0, 1>(M);
+  });
+}
+
+// Gas-kinetic flux in the local frame (normal = first axis).
+//   ql, qr: conservative states on the two sides of the Gauss point
+//   dl[j], dr[j]: their derivatives along the local axes j = n, t1, t2
+// Output: F^n and dF/dt of Eq. expansion-1 (Section 2.2) for step dt.
+template <typename R, bool VISC>
+__device__ void gks_flux(const R ql[5], const R dl[3][5], const R qr[5], const R dr[3][5], R dt,
+                         const FluxParams<R>& P, R F[5], R dF[5]) {
+  const R K = P.Kint;
+  const Prim<R> pl = prim_of(ql, K), pr = prim_of(qr, K);
+  constexpr int NU = VISC ? 7 : 5;
+  Mom<R> Ml, Mr;
+  moments<NU>(pl, +1, K, Ml);
+  moments<NU>(pr, -1, K, Mr);
+
+  // half-space Gram matrices <psi_i psi_j>^(+/-), symmetric
+  R Gl[5][5], Gr[5][5];
+  sfor<5>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    sfor<5>([&](auto J) {
+      constexpr int j = decltype(J)::value;
+      if constexpr (j >= i) {
+        Gl[i][j] = Gl[j][i] = mpsi2<i, j, 0, 0, 0>(Ml);
+        Gr[i][j] = Gr[j][i] = mpsi2<i, j, 0, 0, 0>(Mr);
+      }
+    });
+  });
+  // interface equilibrium Q0 = rho_l <psi>^+_l + rho_r <psi>^-_r
+  R q0[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) q0[i] = pl.rho * Gl[0][i] + pr.rho * Gr[0][i];
+
+  // dQ0/dn_j = int_{u>0} psi a^l_j g_l + int_{u<0} psi a^r_j g_r
+  R dq0[3][5];
+  R al[3][5], ar[3][5];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    micro_slope_rho(pl, K, dl[j], al[j]);  // rho_l a^l_j
+    micro_slope_rho(pr, K, dr[j], ar[j]);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      R s = R(0);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) s += Gl[i][k] * al[j][k] + Gr[i][k] * ar[j][k];
+      dq0[j][i] = s;
+    }
+  }
+  // Euler flux of Q0 and the time derivative of Q0 from the compatibility
+  // condition <abar.u + Abar> = 0:  dQ0/dt = -sum_j J_j(Q0) dQ0/dn_j
+  const EState<R> s0 = estate(q0, P.gamma);
+  R t0[5], t1[5], t2[5], qt[5], Fe[5], Ye[5];
+  euler_jv<0>(s0, dq0[0], t0);
+  euler_jv<1>(s0, dq0[1], t1);
+  euler_jv<2>(s0, dq0[2], t2);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) qt[i] = -(t0[i] + t1[i] + t2[i]);
+  euler_jv<0>(s0, qt, Ye);  // rho0 <u Abar psi>
+  Fe[0] = s0.m[0];
+  Fe[1] = s0.m[0] * s0.u[0] + s0.p;
+  Fe[2] = s0.m[0] * s0.u[1];
+  Fe[3] = s0.m[0] * s0.u[2];
+  Fe[4] = (s0.E + s0.p) * s0.u[0];
+
+  if constexpr (!VISC) {
+    // tau = 0: f = g0 (1 + Abar t)  =>  F^n = rho0 <u psi>, dF/dt = rho0 <u Abar psi>
+#pragma unroll
+    for (int i = 0; i < 5; ++i) { F[i] = Fe[i]; dF[i] = Ye[i]; }
+    return;
+  } else {
+    const Prim<R> p0 = prim_of(q0, K);
+    const R plp = pl.rho * pl.h2, prp = pr.rho * pr.h2, p0p = p0.rho * p0.h2;
+    // collision time: tau = mu(T0)/p0 + C dt |p_l - p_r|/(p_l + p_r), T = p/rho
+    R mu = P.mu_ref;
+    if (P.visc_exp != R(0) && mu != R(0)) mu = P.mu_ref * pow(p0.h2 * R(2) / P.T_ref, P.visc_exp);
+    const R tau = mu / p0p + P.tau_c * dt * fabs(plp - prp) / (plp + prp);
+    if (!(tau > R(0))) {
+#pragma unroll
+      for (int i = 0; i < 5; ++i) { F[i] = Fe[i]; dF[i] = Ye[i]; }
+      return;
+    }
+    // rho0 abar_j and rho0 Abar
+    R ab[3][5];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) micro_slope_rho(p0, K, dq0[j], ab[j]);
+    Mom<R> M0;
+    moments<7>(p0, 0, K, M0);
+    R X0[5];
+    flux_of_slope(M0, ab, X0);  // rho0 <u (abar.u) psi>
+    // side terms: rho_k A^k from <a^k.u + A^k> = 0, full-space moments of g_k
+    R Al[5], Ar[5], tmp[5], s1[5], s2[5];
+    {
+      const EState<R> sl = estate(ql, P.gamma);
+      euler_jv<0>(sl, dl[0], tmp);
+      euler_jv<1>(sl, dl[1], s1);
+      euler_jv<2>(sl, dl[2], s2);
+#pragma unroll
+      for (int i = 0; i < 5; ++i) tmp[i] = -(tmp[i] + s1[i] + s2[i]);
+      micro_slope_rho(pl, K, tmp, Al);
+      const EState<R> sr = estate(qr, P.gamma);
+      euler_jv<0>(sr, dr[0], tmp);
+      euler_jv<1>(sr, dr[1], s1);
+      euler_jv<2>(sr, dr[2], s2);
+#pragma unroll
+      for (int i = 0; i < 5; ++i) tmp[i] = -(tmp[i] + s1[i] + s2[i]);
+      micro_slope_rho(pr, K, tmp, Ar);
+    }
+    R Xl[5], Xr[5], Nk[5], Yk[5];
+    flux_of_slope(Ml, al, Xl);
+    flux_of_slope(Mr, ar, Xr);
+    sfor<5>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      Nk[i] = pl.rho * mpsi<i, 1, 0, 0, 0>(Ml) + pr.rho * mpsi<i, 1, 0, 0, 0>(Mr);
+      R yl = R(0), yr = R(0);
+      sfor<5>([&](auto J) {
+        constexpr int j = decltype(J)::value;
+        yl += Al[j] * mpsi2<i, j, 1, 0, 0>(Ml);
+        yr += Ar[j] * mpsi2<i, j, 1, 0, 0>(Mr);
+      });
+      Yk[i] = yl + yr;
+    });
+    // time-integral coefficients of the fit F = (4 I(dt/2) - I(dt))/dt,
+    // dF = 4 (I(dt) - 2 I(dt/2))/dt^2, with h = dt/2, r = tau/h and
+    // em = 1 - exp(-h/tau)
+    const R h = R(0.5) * dt;
+    const R r = tau / h;
+    const R em = -expm1(-h / tau);
+    const R g = em * (R(2) + em);  // 3 - 4 e^{-h/tau} + e^{-2h/tau}
+    const R C1 = R(1) - R(0.5) * r * g;
+    const R C2 = tau * (r * g - (R(2) - em * em));
+    const R C3 = tau * (R(0.5) * r * g - R(1));
+    const R C4 = R(0.5) * r * g;
+    const R C5 = tau * (r * g - (R(1) - em * em));
+    const R D1 = r * em * em / h;
+    const R D2 = R(2) * r * em * (R(1) - em) - R(2) * r * r * em * em;
+    const R D3 = R(1) - r * r * em * em;
+    const R D4 = -D1;
+    const R D5 = D2;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      const R xk = Xl[i] + Xr[i];
+      F[i] = C1 * Fe[i] + C2 * X0[i] + C3 * Ye[i] + C4 * Nk[i] - C5 * xk - tau * C4 * Yk[i];
+      dF[i] = D1 * Fe[i] + D2 * X0[i] + D3 * Ye[i] + D4 * Nk[i] - D5 * xk - tau * D4 * Yk[i];
+    }
+    // Prandtl-number fix of the energy flux: + (1/Pr - 1) q with q the heat
+    // flux of the first-order equilibrium part, -tau rho0 <c_u c^2/2 (abar.u+Abar)>,
+    // which by the compatibility condition reduces to -tau w.(X0 + Y0),
+    // w = (|U0|^2/2, -U0, -V0, -W0, 1).
+    if (P.Pr != R(1)) {
+      const R qh = -tau * (R(0.5) * (p0.U * p0.U + p0.V * p0.V + p0.W * p0.W) * (X0[0] + Ye[0]) -
+                           p0.U * (X0[1] + Ye[1]) - p0.V * (X0[2] + Ye[2]) - p0.W * (X0[3] + Ye[3]) +
+                           (X0[4] + Ye[4]));
+      F[4] += (R(1) / P.Pr - R(1)) * qh;
+    }
+  }
+}
+
+// Orthonormal completion (t1, t2) of a unit normal n (Duff et al. 2017).
+template <typename R>
+__device__ __forceinline__ void frame(const R n[3], R t1[3], R t2[3]) {
+  const R sg = n[2] >= R(0) ? R(1) : R(-1);
+  const R a = R(-1) / (sg + n[2]);
+  const R b = n[0] * n[1] * a;
+  t1[0] = R(1) + sg * n[0] * n[0] * a;
+  t1[1] = sg * b;
+  t1[2] = -sg * n[0];
+  t2[0] = b;
+  t2[1] = sg + n[1] * n[1] * a;
+  t2[2] = -n[1];
+}
+
+// --------------------------------------------------------------------------
+// boundary states (Section 5.2), conservative variables
+// --------------------------------------------------------------------------
+// Riemann-invariant far field along the outward unit normal n (any frame).
+template <typename R>
+__device__ __forceinline__ void farfield(const R q[5], const R qinf[5], const R n[3], R gamma, R o[5]) {
+  const R gm1 = gamma - R(1);
+  const R ri = R(1) / q[0];
+  const R ui[3] = {q[1] * ri, q[2] * ri, q[3] * ri};
+  const R pi = gm1 * (q[4] - R(0.5) * q[0] * (ui[0] * ui[0] + ui[1] * ui[1] + ui[2] * ui[2]));
+  const R re = qinf[0];
+  const R ue[3] = {qinf[1] / re, qinf[2] / re, qinf[3] / re};
+  const R pe = gm1 * (qinf[4] - R(0.5) * re * (ue[0] * ue[0] + ue[1] * ue[1] + ue[2] * ue[2]));
+  const R ci = sqrt(gamma * pi * ri), ce = sqrt(gamma * pe / re);
+  const R uni = ui[0] * n[0] + ui[1] * n[1] + ui[2] * n[2];
+  const R une = ue[0] * n[0] + ue[1] * n[1] + ue[2] * n[2];
+  if (uni >= ci) {
+    for (int i = 0; i < 5; ++i) o[i] = q[i];
+    return;
+  }
+  if (uni <= -ci) {
+    for (int i = 0; i < 5; ++i) o[i] = qinf[i];
+    return;
+  }
+  const R rp = uni + R(2) * ci / gm1;   // outgoing invariant from the interior
+  const R rm = une - R(2) * ce / gm1;   // incoming invariant from the free stream
+  const R un = R(0.5) * (rp + rm);
+  const R c = R(0.25) * gm1 * (rp - rm);
+  R ent, ut[3];
+  if (un > R(0)) {
+    ent = pi / pow(q[0], gamma);
+    for (int a = 0; a < 3; ++a) ut[a] = ui[a] - uni * n[a];
+  } else {
+    ent = pe / pow(re, gamma);
+    for (int a = 0; a < 3; ++a) ut[a] = ue[a] - une * n[a];
+  }
+  const R rho = pow(c * c / (gamma * ent), R(1) / gm1);
+  const R p = rho * c * c / gamma;
+  R u2 = R(0);
+  for (int a = 0; a < 3; ++a) {
+    const R ua = ut[a] + un * n[a];
+    o[1 + a] = rho * ua;
+    u2 += ua * ua;
+  }
+  o[0] = rho;
+  o[4] = p / gm1 + R(0.5) * rho * u2;
+}
+
+// --------------------------------------------------------------------------
+// kernels
+// --------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
+
+__global__ void k_control(Control* c, double t_end, double dt_fixed) {
+  c->t_end = t_end;
+  c->dt_fixed = dt_fixed;
+}
+
+__global__ void k_reset(Control* c, double t) {
+  c->t = t;
+  c->dt = 0.0;
+  c->steps = 0;
+  c->flags = 0;
+  c->dtmin_bits = dbits(__longlong_as_double(0x7ff0000000000000LL));
+}
+
+__global__ void k_finalize(Control* c, double cfl) {
+  double dt = c->dt_fixed > 0.0 ? c->dt_fixed : cfl * __longlong_as_double((long long)c->dtmin_bits);
+  if (c->t_end > 0.0) dt = fmin(dt, c->t_end - c->t);
+  if (!(dt > 0.0) || !(dt < 1e300)) dt = 0.0;
+  c->dt = dt;
+  if (dt > 0.0) {
+    c->t += dt;
+    c->steps += 1;
+    c->dtmin_bits = dbits(__longlong_as_double(0x7ff0000000000000LL));
+  }
+}
+
+// Local step bound of cell c (without the CFL factor).
+__device__ __forceinline__ double cell_dt(const double q[5], double hdt, const DevParams& P) {
+  const double ri = 1.0 / q[0];
+  const double u = q[1] * ri, v = q[2] * ri, w = q[3] * ri;
+  const double u2 = u * u + v * v + w * w;
+  const double p = (P.gamma - 1.0) * (q[4] - 0.5 * q[0] * u2);
+  const double a = sqrt(P.gamma * p * ri);
+  double dt = hdt / (sqrt(u2) + a);
+  if (P.mu_ref > 0.0) {
+    double mu = P.mu_ref;
+    if (P.visc_exp != 0.0) mu = P.mu_ref * pow(p * ri / P.T_ref, P.visc_exp);
+    dt = fmin(dt, q[0] * hdt * hdt / (2.0 * mu));
+  }
+  return dt;
+}
+
+__device__ __forceinline__ void block_min_to(unsigned long long* dst, double v) {
+  __shared__ double red[kBlock / 32];
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double x = threadIdx.x < kBlock / 32 ? red[threadIdx.x] : __longlong_as_double(0x7ff0000000000000LL);
+    for (int o = 16; o > 0; o >>= 1) x = fmin(x, __shfl_xor_sync(0xffffffffu, x, o));
+    if (threadIdx.x == 0 && x >= 0.0) atomicMin(dst, dbits(x));
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_dt(DevMesh m, DevParams P, const double* __restrict__ Q, Control* c) {
+  const int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  double v = __longlong_as_double(0x7ff0000000000000LL);
+  if (i < m.nc) {
+    double q[5];
+    for (int k = 0; k < 5; ++k) q[k] = Q[k * m.nce + i];
+    v = cell_dt(q, m.hdt[i], P);
+    if (!(v >= 0.0)) v = __longlong_as_double(0x7ff0000000000000LL);
+  }
+  block_min_to(&c->dtmin_bits, v);
+}
+
+// Ghost cell averages: the boundary map of the mirrored interior cell.
+__global__ void __launch_bounds__(kBlock) k_ghost(DevMesh m, DevParams P, double* __restrict__ Q, float* __restrict__ Qf,
+                                                  const Control* __restrict__ c) {
+  const int64_t g = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (g >= m.ng || c->dt == 0.0) return;
+  const int64_t s = m.gsrc[g];
+  double q[5], o[5];
+  for (int k = 0; k < 5; ++k) q[k] = Q[k * m.nce + s];
+  if (m.gtag[g] == 3) {  // wall: momentum reversed
+    o[0] = q[0]; o[1] = -q[1]; o[2] = -q[2]; o[3] = -q[3]; o[4] = q[4];
+  } else {
+    const double n[3] = {m.gnrm[g], m.gnrm[m.ng + g], m.gnrm[2 * m.ng + g]};
+    farfield(q, P.qinf, n, P.gamma, o);
+  }
+  for (int k = 0; k < 5; ++k) {
+    Q[k * m.nce + m.nc + g] = o[k];
+    if (Qf) Qf[k * m.nce + m.nc + g] = (float)o[k];
+  }
+}
+
+// WENO reconstruction, one thread per cell.  Output coef[(v*10+j)*nc + c]:
+// the combined polynomial P(x) = q + g.d + sum k_ab d_a d_b, d = x - centroid,
+// j = 0: q, 1-3: g, 4-9: k_xx k_yy k_zz k_xy k_yz k_zx.
+// The stencil differences live in dynamic shared memory, sdq[(k*5+v)*kRecon + t],
+// because the sub-stencil members are addressed by per-cell indices.
+constexpr int kRecon = 64;
+
+template <typename Real, typename QT, int K, int M, int KM>
+__global__ void __launch_bounds__(kRecon) k_recon(DevMesh m, DevParams P, const QT* __restrict__ Q,
+                                                  Real* __restrict__ coef, const Control* __restrict__ ctl) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* sdq = reinterpret_cast<Real*>(smem_raw);
+  const int64_t nc = m.nc;
+  const int64_t c = (int64_t)blockIdx.x * kRecon + threadIdx.x;
+  if (c >= nc || ctl->dt == 0.0) return;
+  const int t = threadIdx.x;
+  Real qi[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) qi[v] = (Real)Q[v * m.nce + c];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int64_t j = m.sten[k * nc + c];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sdq[(k * 5 + v) * kRecon + t] = (Real)Q[v * m.nce + j] - qi[v];
+  }
+  Real mi[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) mi[q] = (Real)m.mom[q * nc + c];
+  const Real hi = (Real)m.hinv[c];
+  const Real glin = (Real)P.glin, g0 = Real(1) - Real(M) * glin, eps = (Real)P.eps;
+  uint8_t sidx[M * KM];
+#pragma unroll
+  for (int r = 0; r < M * KM; ++r) sidx[r] = m.subidx[r * nc + c];
+
+#pragma unroll 1
+  for (int v = 0; v < 5; ++v) {
+    Real a[9];
+#pragma unroll
+    for (int d = 0; d < 9; ++d) {
+      Real s = Real(0);
+#pragma unroll
+      for (int k = 0; k < K; ++k) s += (Real)m.pinv0[(d * K + k) * nc + c] * sdq[(k * 5 + v) * kRecon + t];
+      a[d] = s;
+    }
+    Real b[M][3];
+#pragma unroll
+    for (int s = 0; s < M; ++s)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        Real acc = Real(0);
+#pragma unroll
+        for (int r = 0; r < KM; ++r)
+          acc += (Real)m.pinvm[((s * 3 + d) * KM + r) * nc + c] * sdq[(sidx[s * KM + r] * 5 + v) * kRecon + t];
+        b[s][d] = acc;
+      }
+    // smoothness indicators (scaled coordinates; the |cell| powers cancel):
+    // beta_0 = sum_a (a_a^2 + H_a.Mi.H_a) + sum_{|l|=2} (d^l P0)^2, beta_m = |b_m|^2
+    const Real H[3][3] = {{Real(2) * a[3], a[6], a[8]}, {a[6], Real(2) * a[4], a[7]}, {a[8], a[7], Real(2) * a[5]}};
+    Real beta0 = Real(0);
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      const Real h0 = H[x][0], h1 = H[x][1], h2 = H[x][2];
+      const Real quad = h0 * (mi[0] * h0 + mi[3] * h1 + mi[5] * h2) + h1 * (mi[3] * h0 + mi[1] * h1 + mi[4] * h2) +
+                        h2 * (mi[5] * h0 + mi[4] * h1 + mi[2] * h2);
+      beta0 += a[x] * a[x] + quad;
+    }
+    beta0 += H[0][0] * H[0][0] + H[1][1] * H[1][1] + H[2][2] * H[2][2] + a[6] * a[6] + a[7] * a[7] + a[8] * a[8];
+    Real beta[M];
+    Real tz = Real(0);
+#pragma unroll
+    for (int s = 0; s < M; ++s) {
+      beta[s] = b[s][0] * b[s][0] + b[s][1] * b[s][1] + b[s][2] * b[s][2];
+      tz += fabs(beta0 - beta[s]);
+    }
+    tz *= Real(1) / Real(M);
+    // WENO-Z type weights
+    Real w0 = g0 * (Real(1) + tz / (beta0 + eps));
+    Real w[M];
+    Real wsum = w0;
+#pragma unroll
+    for (int s = 0; s < M; ++s) {
+      w[s] = glin * (Real(1) + tz / (beta[s] + eps));
+      wsum += w[s];
+    }
+    const Real winv = Real(1) / wsum;
+    const Real c0 = w0 * winv / g0;  // wbar_0 / gamma_0
+    Real lin[3] = {c0 * a[0], c0 * a[1], c0 * a[2]};
+#pragma unroll
+    for (int s = 0; s < M; ++s) {
+      const Real cm = w[s] * winv - c0 * glin;  // wbar_m - wbar_0 gamma_m / gamma_0
+#pragma unroll
+      for (int d = 0; d < 3; ++d) lin[d] += cm * b[s][d];
+    }
+    Real quad[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) quad[q] = c0 * a[3 + q];
+    // to physical units about the centroid; the zero-mean basis shifts the constant
+    Real q0 = qi[v];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) q0 -= quad[q] * mi[q];
+    Real* out = coef + (int64_t)v * 10 * nc + c;
+    out[0] = q0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) out[(1 + d) * nc] = lin[d] * hi;
+    const Real hi2 = hi * hi;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) out[(4 + q) * nc] = quad[q] * hi2;
+  }
+}
+
+// Point value and gradient of the combined polynomial of cell c at offset d.
+template <typename Real>
+__device__ __forceinline__ void eval_poly(const Real* __restrict__ coef, int64_t nc, int64_t c, const Real d[3],
+                                          Real val[5], Real grad[5][3]) {
+  const Real dxx = d[0] * d[0], dyy = d[1] * d[1], dzz = d[2] * d[2];
+  const Real dxy = d[0] * d[1], dyz = d[1] * d[2], dzx = d[2] * d[0];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const Real* p = coef + (int64_t)v * 10 * nc + c;
+    const Real q = p[0], gx = p[nc], gy = p[2 * nc], gz = p[3 * nc];
+    const Real kxx = p[4 * nc], kyy = p[5 * nc], kzz = p[6 * nc], kxy = p[7 * nc], kyz = p[8 * nc], kzx = p[9 * nc];
+    val[v] = q + gx * d[0] + gy * d[1] + gz * d[2] + kxx * dxx + kyy * dyy + kzz * dzz + kxy * dxy + kyz * dyz +
+             kzx * dzx;
+    grad[v][0] = gx + Real(2) * kxx * d[0] + kxy * d[1] + kzx * d[2];
+    grad[v][1] = gy + Real(2) * kyy * d[1] + kxy * d[0] + kyz * d[2];
+    grad[v][2] = gz + Real(2) * kzz * d[2] + kyz * d[1] + kzx * d[0];
+  }
+}
+
+// Face flux, one thread per face: sum over the Gauss points of weight*area
+// times the flux of Eq. (flux), F and dF/dt in the global frame, oriented
+// from the owner to the neighbour.  Output Fs[j*nf + f], j = 0..4 F, 5..9 dF.
+template <typename Real, int G, bool VISC>
+__global__ void __launch_bounds__(kBlock) k_flux(DevMesh m, DevParams P, const Real* __restrict__ coef,
+                                                 Real* __restrict__ Fs, const Control* __restrict__ ctl) {
+  const int64_t nf = m.nf, nc = m.nc;
+  const int64_t f = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  const double dtd = ctl->dt;
+  if (f >= nf || dtd == 0.0) return;
+  const Real dt = (Real)dtd;
+  FluxParams<Real> FP;
+  FP.gamma = (Real)P.gamma;
+  FP.Kint = (Real)P.Kint;
+  FP.mu_ref = (Real)P.mu_ref;
+  FP.T_ref = (Real)P.T_ref;
+  FP.visc_exp = (Real)P.visc_exp;
+  FP.Pr = (Real)P.Pr;
+  FP.tau_c = (Real)P.tau_c;
+  const int64_t own = m.fown[f];
+  const int nbr = m.fnbr[f];
+  Real Fa[5] = {0, 0, 0, 0, 0}, Da[5] = {0, 0, 0, 0, 0};
+#pragma unroll 1
+  for (int g = 0; g < G; ++g) {
+    Real n[3], d[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      n[a] = (Real)m.fn[(g * 3 + a) * nf + f];
+      d[a] = (Real)m.fdl[(g * 3 + a) * nf + f];
+    }
+    const Real wgt = (Real)m.fw[g * nf + f];
+    Real t1[3], t2[3];
+    frame(n, t1, t2);
+    Real qv[5], gr[5][3];
+    eval_poly(coef, nc, own, d, qv, gr);
+    // local frame: rotate momentum, take derivatives along n, t1, t2
+    Real ql[5], dl[3][5], qr[5], dr[3][5];
+    auto rot = [&](const Real x[5], Real y[5]) {
+      y[0] = x[0];
+      y[1] = x[1] * n[0] + x[2] * n[1] + x[3] * n[2];
+      y[2] = x[1] * t1[0] + x[2] * t1[1] + x[3] * t1[2];
+      y[3] = x[1] * t2[0] + x[2] * t2[1] + x[3] * t2[2];
+      y[4] = x[4];
+    };
+    auto local = [&](const Real q[5], const Real gg[5][3], Real qo[5], Real dd[3][5]) {
+      rot(q, qo);
+      Real tmp[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) tmp[v] = gg[v][0] * n[0] + gg[v][1] * n[1] + gg[v][2] * n[2];
+      rot(tmp, dd[0]);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) tmp[v] = gg[v][0] * t1[0] + gg[v][1] * t1[1] + gg[v][2] * t1[2];
+      rot(tmp, dd[1]);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) tmp[v] = gg[v][0] * t2[0] + gg[v][1] * t2[1] + gg[v][2] * t2[2];
+      rot(tmp, dd[2]);
+    };
+    local(qv, gr, ql, dl);
+    if (nbr >= 0) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) d[a] = (Real)m.fdr[(g * 3 + a) * nf + f];
+      eval_poly(coef, nc, (int64_t)nbr, d, qv, gr);
+      local(qv, gr, qr, dr);
+    } else if (nbr == -3) {
+      // no-slip adiabatic wall: mirror state, momentum reversed, normal
+      // derivative reflected
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const Real sg = (v >= 1 && v <= 3) ? Real(-1) : Real(1);
+        qr[v] = sg * ql[v];
+        dr[0][v] = -sg * dl[0][v];
+        dr[1][v] = sg * dl[1][v];
+        dr[2][v] = sg * dl[2][v];
+      }
+    } else {
+      // Riemann-invariant far field, evaluated in the local frame, zero gradient
+      Real qinf[5], qil[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) qinf[v] = (Real)P.qinf[v];
+      rot(qinf, qil);
+      const Real ex[3] = {Real(1), Real(0), Real(0)};
+      farfield(ql, qil, ex, FP.gamma, qr);
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int v = 0; v < 5; ++v) dr[j][v] = Real(0);
+    }
+    Real Fl[5], Dl[5];
+    gks_flux<Real, VISC>(ql, dl, qr, dr, dt, FP, Fl, Dl);
+    // back to the global frame, weighted by the quadrature weight times area
+    Fa[0] += wgt * Fl[0];
+    Da[0] += wgt * Dl[0];
+    Fa[4] += wgt * Fl[4];
+    Da[4] += wgt * Dl[4];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      Fa[1 + a] += wgt * (Fl[1] * n[a] + Fl[2] * t1[a] + Fl[3] * t2[a]);
+      Da[1 + a] += wgt * (Dl[1] * n[a] + Dl[2] * t1[a] + Dl[3] * t2[a]);
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    Fs[v * nf + f] = Fa[v];
+    Fs[(5 + v) * nf + f] = Da[v];
+  }
+}
+
+// Gather of the face fluxes into L and dL/dt of cell c (Eq. finite).
+template <typename Real, int NFC>
+__device__ __forceinline__ void gather(const DevMesh& m, const Real* __restrict__ Fs, int64_t c, double L[5],
+                                       double dL[5]) {
+  for (int v = 0; v < 5; ++v) L[v] = dL[v] = 0.0;
+#pragma unroll
+  for (int p = 0; p < NFC; ++p) {
+    const int32_t e = m.cface[p * m.nc + c];
+    const int64_t f = e >> 1;
+    const double sg = (e & 1) ? -1.0 : 1.0;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      L[v] += sg * (double)Fs[v * m.nf + f];
+      dL[v] += sg * (double)Fs[(5 + v) * m.nf + f];
+    }
+  }
+  const double vi = -m.volinv[c];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) { L[v] *= vi; dL[v] *= vi; }
+}
+
+// Stage 1: Q* = Q + dt/2 L + dt^2/8 dL;  R = Q + dt L + dt^2/6 dL.
+template <typename Real, int NFC>
+__global__ void __launch_bounds__(kBlock) k_update1(DevMesh m, const Real* __restrict__ Fs, const double* __restrict__ Q,
+                                                   double* __restrict__ Qs, double* __restrict__ R,
+                                                   float* __restrict__ Qf, const Control* __restrict__ ctl) {
+  const int64_t c = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  const double dt = ctl->dt;
+  if (c >= m.nc || dt == 0.0) return;
+  double L[5], dL[5];
+  gather<Real, NFC>(m, Fs, c, L, dL);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const double q = Q[v * m.nce + c];
+    const double qs = q + 0.5 * dt * L[v] + 0.125 * dt * dt * dL[v];
+    Qs[v * m.nce + c] = qs;
+    R[v * m.nc + c] = q + dt * L[v] + dt * dt / 6.0 * dL[v];
+    if (Qf) Qf[v * m.nce + c] = (float)qs;
+  }
+}
+
+// Stage 2: Q^{n+1} = R + dt^2/3 dL(Q*); next step bound; non-finite flag.
+template <typename Real, int NFC>
+__global__ void __launch_bounds__(kBlock) k_update2(DevMesh m, DevParams P, const Real* __restrict__ Fs,
+                                                   double* __restrict__ Q, const double* __restrict__ R,
+                                                   float* __restrict__ Qf, Control* __restrict__ ctl) {
+  const int64_t c = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  const double dt = ctl->dt;
+  if (dt == 0.0) return;  // uniform across the grid: no thread reaches the block reduction
+  double bound = __longlong_as_double(0x7ff0000000000000LL);
+  if (c < m.nc) {
+    double L[5], dL[5];
+    gather<Real, NFC>(m, Fs, c, L, dL);
+    double q[5];
+    bool finite = true;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      q[v] = R[v * m.nc + c] + dt * dt / 3.0 * dL[v];
+      finite = finite && isfinite(q[v]);
+      Q[v * m.nce + c] = q[v];
+      if (Qf) Qf[v * m.nce + c] = (float)q[v];
+    }
+    if (!finite) atomicOr(&ctl->flags, FLAG_NONFINITE);
+    bound = cell_dt(q, m.hdt[c], P);
+    if (!(bound >= 0.0)) bound = __longlong_as_double(0x7ff0000000000000LL);
+  }
+  block_min_to(&ctl->dtmin_bits, bound);
+}
+
+// Binary32 copy of the state (mixed precision).
+__global__ void k_tofloat(const double* __restrict__ Q, float* __restrict__ Qf, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (i < n) Qf[i] = (float)Q[i];
+}
+
+__global__ void k_setdt(Control* c, double dt) { c->dt = dt; }
+
+// L and dL/dt of the state (test path).
+template <typename Real, int NFC>
+__global__ void k_operator(DevMesh m, const Real* __restrict__ Fs, double* __restrict__ L, double* __restrict__ dL) {
+  const int64_t c = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (c >= m.nc) return;
+  double a[5], b[5];
+  gather<Real, NFC>(m, Fs, c, a, b);
+  for (int v = 0; v < 5; ++v) { L[v * m.nc + c] = a[v]; dL[v * m.nc + c] = b[v]; }
+}
+
+inline unsigned blocks(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+
+// Stencil shapes compiled in: tets (K up to 16, 4 sub-stencils of 6),
+// hexes (K up to 24, 8 octants of 3).
+// prep = true only opts the instantiation in to its dynamic shared memory size
+// (above 48 KB for FP64 hexahedra); this happens at solver creation, before
+// any stream capture.
+template <typename Real, typename QT, int K, int M, int KM>
+void recon_launch(const DevMesh& m, const DevParams& p, const QT* Q, Real* coef, const Control* ctl, cudaStream_t s,
+                  bool prep) {
+  const size_t smem = sizeof(Real) * K * 5 * kRecon;
+  if (prep) {
+    cudaFuncSetAttribute(k_recon<Real, QT, K, M, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return;
+  }
+  const unsigned nb = (unsigned)((m.nc + kRecon - 1) / kRecon);
+  k_recon<Real, QT, K, M, KM><<<nb, kRecon, smem, s>>>(m, p, Q, coef, ctl);
+}
+
+// Stencil shapes compiled in: tetrahedra with 12..16 members and 4 sub-stencils
+// of up to 6; hexahedra with 18..24 members and 8 octants of 3.
+template <typename Real, typename QT, int M, int KM>
+void recon_dispatch(const DevMesh& m, const DevParams& p, const QT* Q, Real* coef, const Control* ctl, cudaStream_t s,
+                    bool prep) {
+  switch (m.K) {
+    case 12: recon_launch<Real, QT, 12, M, KM>(m, p, Q, coef, ctl, s, prep); break;
+    case 13: recon_launch<Real, QT, 13, M, KM>(m, p, Q, coef, ctl, s, prep); break;
+    case 14: recon_launch<Real, QT, 14, M, KM>(m, p, Q, coef, ctl, s, prep); break;
+    case 15: recon_launch<Real, QT, 15, M, KM>(m, p, Q, coef, ctl, s, prep); break;
+    case 16: recon_launch<Real, QT, 16, M, KM>(m, p, Q, coef, ctl, s, prep); break;
+    default: break;
+  }
+}
+template <typename Real, typename QT>
+void recon_hex(const DevMesh& m, const DevParams& p, const QT* Q, Real* coef, const Control* ctl, cudaStream_t s,
+               bool prep) {
+  switch (m.K) {
+    case 18: recon_launch<Real, QT, 18, 8, 3>(m, p, Q, coef, ctl, s, prep); break;
+    case 20: recon_launch<Real, QT, 20, 8, 3>(m, p, Q, coef, ctl, s, prep); break;
+    case 22: recon_launch<Real, QT, 22, 8, 3>(m, p, Q, coef, ctl, s, prep); break;
+    case 24: recon_launch<Real, QT, 24, 8, 3>(m, p, Q, coef, ctl, s, prep); break;
+    default: break;
+  }
+}
+
+// Stencil sizes the kernels are compiled for.
+}  // namespace
+bool stencil_supported(int nfc, int K) {
+  if (nfc == 4) return K >= 12 && K <= 16;
+  return K == 18 || K == 20 || K == 22 || K == 24;
+}
+namespace {
+
+template <typename Real, typename QT>
+void recon_any(const DevMesh& m, const DevParams& p, const QT* Q, Real* coef, const Control* ctl, cudaStream_t s,
+               bool prep = false) {
+  if (m.M == 4) recon_dispatch<Real, QT, 4, 6>(m, p, Q, coef, ctl, s, prep);
+  else recon_hex<Real, QT>(m, p, Q, coef, ctl, s, prep);
+}
+
+template <typename Real>
+void flux_any(const DevMesh& m, const DevParams& p, const Real* coef, Real* Fs, const Control* ctl, cudaStream_t s) {
+  const unsigned nb = blocks(m.nf);
+  if (m.G == 3) {
+    if (p.viscous) k_flux<Real, 3, true><<<nb, kBlock, 0, s>>>(m, p, coef, Fs, ctl);
+    else k_flux<Real, 3, false><<<nb, kBlock, 0, s>>>(m, p, coef, Fs, ctl);
+  } else {
+    if (p.viscous) k_flux<Real, 4, true><<<nb, kBlock, 0, s>>>(m, p, coef, Fs, ctl);
+    else k_flux<Real, 4, false><<<nb, kBlock, 0, s>>>(m, p, coef, Fs, ctl);
+  }
+}
+
+template <typename Real>
+void stage_pair(const DevMesh& m, const DevParams& p, const DevWork& w, bool mixed, cudaStream_t s,
+                const StepEvents* ev) {
+  Real* coef = static_cast<Real*>(w.coef);
+  Real* Fs = static_cast<Real*>(w.Fs);
+  const unsigned nbc = blocks(m.nc);
+  float* Qf = mixed ? w.Qf : nullptr;
+  auto mark = [&](int i) { if (ev) cudaEventRecord(ev->ev[i], s); };
+  // stage 1 on Q^n
+  if (m.ng) k_ghost<<<blocks(m.ng), kBlock, 0, s>>>(m, p, w.Q, Qf, w.ctl);
+  if (mixed) recon_any<Real, float>(m, p, w.Qf, coef, w.ctl, s);
+  else recon_any<Real, double>(m, p, w.Q, coef, w.ctl, s);
+  mark(2);
+  flux_any<Real>(m, p, coef, Fs, w.ctl, s);
+  mark(3);
+  if (m.nfc == 4) k_update1<Real, 4><<<nbc, kBlock, 0, s>>>(m, Fs, w.Q, w.Qs, w.R, Qf, w.ctl);
+  else k_update1<Real, 6><<<nbc, kBlock, 0, s>>>(m, Fs, w.Q, w.Qs, w.R, Qf, w.ctl);
+  mark(4);
+  // stage 2 on Q*
+  if (m.ng) k_ghost<<<blocks(m.ng), kBlock, 0, s>>>(m, p, w.Qs, Qf, w.ctl);
+  if (mixed) recon_any<Real, float>(m, p, w.Qf, coef, w.ctl, s);
+  else recon_any<Real, double>(m, p, w.Qs, coef, w.ctl, s);
+  mark(5);
+  flux_any<Real>(m, p, coef, Fs, w.ctl, s);
+  mark(6);
+  if (m.nfc == 4) k_update2<Real, 4><<<nbc, kBlock, 0, s>>>(m, p, Fs, w.Q, w.R, Qf, w.ctl);
+  else k_update2<Real, 6><<<nbc, kBlock, 0, s>>>(m, p, Fs, w.Q, w.R, Qf, w.ctl);
+  mark(7);
+}
+
+}  // namespace
+
+void prepare_kernels(const DevMesh& m, int precision) {
+  if (precision == 1) recon_any<float, float>(m, DevParams{}, nullptr, nullptr, nullptr, 0, true);
+  else recon_any<double, double>(m, DevParams{}, nullptr, nullptr, nullptr, 0, true);
+}
+
+void launch_control(const DevWork& w, double t_end, double dt_fixed, cudaStream_t s) {
+  k_control<<<1, 1, 0, s>>>(w.ctl, t_end, dt_fixed);
+}
+
+void launch_reset(const DevMesh& m, const DevParams& p, const DevWork& w, int precision, double t, cudaStream_t s) {
+  k_reset<<<1, 1, 0, s>>>(w.ctl, t);
+  if (precision == 1) k_tofloat<<<blocks(5 * m.nce), kBlock, 0, s>>>(w.Q, w.Qf, 5 * m.nce);
+  k_dt<<<blocks(m.nc), kBlock, 0, s>>>(m, p, w.Q, w.ctl);
+}
+
+void launch_step(const DevMesh& m, const DevParams& p, const DevWork& w, int precision, cudaStream_t s,
+                 const StepEvents* ev) {
+  if (ev) cudaEventRecord(ev->ev[0], s);
+  k_finalize<<<1, 1, 0, s>>>(w.ctl, p.cfl);
+  if (ev) cudaEventRecord(ev->ev[1], s);
+  if (precision == 1) stage_pair<float>(m, p, w, true, s, ev);
+  else stage_pair<double>(m, p, w, false, s, ev);
+}
+
+void launch_operator(const DevMesh& m, const DevParams& p, const DevWork& w, int precision, double dt, double* L,
+                     double* dL, cudaStream_t s) {
+  k_setdt<<<1, 1, 0, s>>>(w.ctl, dt);
+  const bool mixed = precision == 1;
+  float* Qf = mixed ? w.Qf : nullptr;
+  if (m.ng) k_ghost<<<blocks(m.ng), kBlock, 0, s>>>(m, p, w.Q, Qf, w.ctl);
+  if (mixed) {
+    recon_any<float, float>(m, p, w.Qf, static_cast<float*>(w.coef), w.ctl, s);
+    flux_any<float>(m, p, static_cast<float*>(w.coef), static_cast<float*>(w.Fs), w.ctl, s);
+    if (m.nfc == 4) k_operator<float, 4><<<blocks(m.nc), kBlock, 0, s>>>(m, static_cast<float*>(w.Fs), L, dL);
+    else k_operator<float, 6><<<blocks(m.nc), kBlock, 0, s>>>(m, static_cast<float*>(w.Fs), L, dL);
+  } else {
+    recon_any<double, double>(m, p, w.Q, static_cast<double*>(w.coef), w.ctl, s);
+    flux_any<double>(m, p, static_cast<double*>(w.coef), static_cast<double*>(w.Fs), w.ctl, s);
+    if (m.nfc == 4) k_operator<double, 4><<<blocks(m.nc), kBlock, 0, s>>>(m, static_cast<double*>(w.Fs), L, dL);
+    else k_operator<double, 6><<<blocks(m.nc), kBlock, 0, s>>>(m, static_cast<double*>(w.Fs), L, dL);
+  }
+}
+
+}  // namespace hgks

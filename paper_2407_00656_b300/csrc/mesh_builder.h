@@ -1,0 +1,66 @@
+// mesh_builder.h -- host-side mesh preprocessing for the HGKS GPU path.
+//
+// Produces the structure-of-arrays data that the kernels read: cells ordered
+// along a Morton curve, faces ordered by owner, boundary ghost slots, padded
+// two-layer WENO stencils with their least-squares pseudo-inverses
+// (Section 2.3, Algorithm 1) and face Gauss-point geometry (Section 2.1).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "hgks.h"
+
+namespace hgks {
+
+struct HostMesh {
+  int ctype = 0;   // 4 or 8 nodes per cell
+  int nfc = 0;     // faces per cell: 4 or 6
+  int G = 0;       // Gauss points per face: 3 or 4
+  int M = 0;       // sub-stencils per cell: 4 or 8
+  int KM = 0;      // padded sub-stencil size: 6 (tet) or 3 (hex)
+  int K = 0;       // padded big-stencil size (max over cells)
+  int64_t nc = 0, nf = 0, ng = 0;
+
+  // cell order: new index -> caller index
+  std::vector<int64_t> perm;
+
+  // Every array is structure-of-arrays: component j of item i at [j*n + i]
+  // (n = nc, ng or nf), so that consecutive threads read consecutive words.
+
+  // per cell, new order
+  std::vector<double> vol;       // [nc]
+  std::vector<double> hdt;       // [nc] 3|cell|/|surface|
+  std::vector<double> cen;       // [3][nc]
+  std::vector<double> mom;       // [6][nc] central second moments / h^2 (xx yy zz xy yz zx)
+  std::vector<double> hinv;      // [nc] 1/h, h = |cell|^(1/3)
+  std::vector<int32_t> sten;     // [K][nc] indices into cells+ghosts (padding: the cell itself)
+  std::vector<double> pinv0;     // [9*K][nc] quadratic least-squares inverse, row d col k at d*K+k
+  std::vector<uint8_t> subidx;   // [M*KM][nc] positions in the big stencil
+  std::vector<double> pinvm;     // [M*3*KM][nc] linear inverses, (m,d,r) at (m*3+d)*KM+r
+  std::vector<int32_t> cface;    // [nfc][nc] 2*face + (1 if the cell is the face's neighbour)
+
+  // per ghost (one per physical boundary face)
+  std::vector<int32_t> gsrc;     // [ng] mirrored interior cell
+  std::vector<int32_t> gtag;     // [ng] HGKS_BC_FARFIELD or HGKS_BC_WALL
+  std::vector<double> gnrm;      // [3][ng] unit outward normal of the mirror plane
+
+  // per face, ordered by owner
+  std::vector<int32_t> fown;     // [nf]
+  std::vector<int32_t> fnbr;     // [nf] neighbour cell, or -tag for a physical boundary
+  std::vector<double> fdl;       // [G*3][nf] Gauss point minus owner centroid
+  std::vector<double> fdr;       // [G*3][nf] Gauss point (neighbour image) minus neighbour centroid
+  std::vector<double> fn;        // [G*3][nf] unit normal, owner -> neighbour
+  std::vector<double> fw;        // [G][nf] quadrature weight times area
+};
+
+// Build from a validated description; returns HGKS_OK or an error code with
+// a message in err.
+int build_host_mesh(const hgks_mesh_desc& d, HostMesh& m, std::string& err);
+
+// Device bytes a solver for this mesh allocates (precision HGKS_FP64 or
+// HGKS_FP32_MIXED), including alignment padding.
+int64_t device_bytes(const HostMesh& m, int precision);
+
+}  // namespace hgks

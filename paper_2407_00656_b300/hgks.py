@@ -1,0 +1,245 @@
+"""ctypes binding of libhgks (include/hgks.h): the same entry points, with
+argument marshalling only.  Every step of the scheme runs in the library's
+CUDA kernels; nothing here computes.
+
+The library is loaded from this package directory (``libhgks.so``, built by
+``paper_2407_00656_b300.build``).  A missing library raises ImportError at
+first use: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhgks.so")
+
+HGKS_OK, HGKS_EINVAL, HGKS_ENOMEM, HGKS_EMESH, HGKS_ECUDA, HGKS_ENONFINITE, HGKS_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+HGKS_TET4, HGKS_HEX8 = 4, 8
+HGKS_BC_PERIODIC, HGKS_BC_FARFIELD, HGKS_BC_WALL = 1, 2, 3
+HGKS_FP64, HGKS_FP32_MIXED = 0, 1
+
+_ERRNAMES = {0: "HGKS_OK", -1: "HGKS_EINVAL", -2: "HGKS_ENOMEM", -3: "HGKS_EMESH", -4: "HGKS_ECUDA",
+             -5: "HGKS_ENONFINITE", -6: "HGKS_ETIMEOUT"}
+
+
+class hgks_mesh_desc(C.Structure):
+    _fields_ = [
+        ("n_nodes", C.c_int64),
+        ("xyz", C.POINTER(C.c_double)),
+        ("n_cells", C.c_int64),
+        ("cell_type", C.c_int32),
+        ("sfc_reorder", C.c_int32),
+        ("cell_nodes", C.POINTER(C.c_int64)),
+        ("n_bfaces", C.c_int64),
+        ("bface_nodes", C.POINTER(C.c_int64)),
+        ("bface_tag", C.POINTER(C.c_int32)),
+        ("periods", C.POINTER(C.c_double)),
+    ]
+
+
+class hgks_params(C.Structure):
+    _fields_ = [
+        ("gamma", C.c_double), ("mu_ref", C.c_double), ("T_ref", C.c_double), ("visc_exp", C.c_double),
+        ("Pr", C.c_double), ("cfl", C.c_double), ("tau_num_c", C.c_double), ("weno_eps", C.c_double),
+        ("weno_gamma_lin", C.c_double), ("q_inf", C.c_double * 5), ("precision", C.c_int32),
+        ("use_graph", C.c_int32), ("stream", C.c_void_p),
+    ]
+
+
+class HGKSError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: {_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+_lock = threading.Lock()
+EXPORTS = ("hgks_params_default", "hgks_mesh_create", "hgks_mesh_destroy", "hgks_mesh_info", "hgks_init",
+           "hgks_write", "hgks_step", "hgks_sync", "hgks_read", "hgks_stage_operator", "hgks_profile",
+           "hgks_destroy", "hgks_last_error")
+
+
+def lib():
+    """Load libhgks.so (raises ImportError when it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"libhgks.so not found at {LIB_PATH}; run python -m paper_2407_00656_b300.build")
+            L = C.CDLL(LIB_PATH)
+            vp, dp = C.c_void_p, C.POINTER(C.c_double)
+            L.hgks_params_default.argtypes = [C.POINTER(hgks_params)]
+            L.hgks_params_default.restype = None
+            L.hgks_mesh_create.argtypes = [C.POINTER(hgks_mesh_desc), C.POINTER(vp)]
+            L.hgks_mesh_destroy.argtypes = [vp]
+            L.hgks_mesh_destroy.restype = None
+            L.hgks_mesh_info.argtypes = [vp, C.c_int]
+            L.hgks_mesh_info.restype = C.c_int64
+            L.hgks_init.argtypes = [vp, C.POINTER(hgks_params), dp, C.POINTER(vp)]
+            L.hgks_write.argtypes = [vp, dp, C.c_double]
+            L.hgks_step.argtypes = [vp, C.c_int, C.c_double, C.c_double]
+            L.hgks_sync.argtypes = [vp]
+            L.hgks_read.argtypes = [vp, dp, dp, C.POINTER(C.c_int64)]
+            L.hgks_stage_operator.argtypes = [vp, C.c_double, dp, dp]
+            L.hgks_profile.argtypes = [vp, C.c_int, C.c_double, C.c_double, dp]
+            L.hgks_destroy.argtypes = [vp]
+            L.hgks_destroy.restype = None
+            L.hgks_last_error.restype = C.c_char_p
+            for name in ("hgks_mesh_create", "hgks_init", "hgks_write", "hgks_step", "hgks_sync", "hgks_read",
+                         "hgks_stage_operator", "hgks_profile"):
+                getattr(L, name).restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _check(rc: int, where: str):
+    if rc != HGKS_OK:
+        raise HGKSError(rc, where, lib().hgks_last_error().decode())
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def params_default() -> hgks_params:
+    p = hgks_params()
+    lib().hgks_params_default(C.byref(p))
+    return p
+
+
+def make_params(**kw) -> hgks_params:
+    """hgks_params with defaults overridden by keyword (q_inf a 5-sequence)."""
+    p = params_default()
+    for k, v in kw.items():
+        if k == "q_inf":
+            for i in range(5):
+                p.q_inf[i] = float(v[i])
+        elif k == "stream":
+            p.stream = C.c_void_p(v)
+        else:
+            setattr(p, k, v)
+    return p
+
+
+class Mesh:
+    """hgks_mesh_create / hgks_mesh_destroy."""
+
+    def __init__(self, xyz, cells, periods=None, bface_nodes=None, bface_tag=None, sfc_reorder: bool = True):
+        self._keep = []
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        cells = np.ascontiguousarray(cells, dtype=np.int64)
+        d = hgks_mesh_desc()
+        d.n_nodes = len(xyz)
+        d.xyz = _dp(xyz)
+        d.n_cells = len(cells)
+        d.cell_type = cells.shape[1]
+        d.sfc_reorder = 1 if sfc_reorder else 0
+        d.cell_nodes = cells.ctypes.data_as(C.POINTER(C.c_int64))
+        self._keep += [xyz, cells]
+        if bface_nodes is not None and len(bface_nodes):
+            bfn = np.asarray(bface_nodes, dtype=np.int64)
+            if bfn.shape[1] == 3:
+                bfn = np.concatenate([bfn, -np.ones((len(bfn), 1), dtype=np.int64)], axis=1)
+            bfn = np.ascontiguousarray(bfn)
+            bft = np.ascontiguousarray(bface_tag, dtype=np.int32)
+            d.n_bfaces = len(bfn)
+            d.bface_nodes = bfn.ctypes.data_as(C.POINTER(C.c_int64))
+            d.bface_tag = bft.ctypes.data_as(C.POINTER(C.c_int32))
+            self._keep += [bfn, bft]
+        if periods is not None:
+            per = np.ascontiguousarray(periods, dtype=np.float64)
+            d.periods = _dp(per)
+            self._keep.append(per)
+        h = C.c_void_p()
+        _check(lib().hgks_mesh_create(C.byref(d), C.byref(h)), "hgks_mesh_create")
+        self._h = h
+        self._keep = []
+
+    def info(self, what: int) -> int:
+        return int(lib().hgks_mesh_info(self._h, what))
+
+    @property
+    def n_cells(self):
+        return self.info(0)
+
+    @property
+    def n_faces(self):
+        return self.info(1)
+
+    @property
+    def n_ghosts(self):
+        return self.info(2)
+
+    @property
+    def stencil_size(self):
+        return self.info(3)
+
+    def device_bytes(self, precision: int = HGKS_FP64) -> int:
+        return self.info(5 if precision == HGKS_FP64 else 6)
+
+    def release(self):
+        """Hand ownership to a solver (hgks_init took it)."""
+        h, self._h = self._h, None
+        return h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().hgks_mesh_destroy(h)
+            self._h = None
+
+
+class Solver:
+    """hgks_init / hgks_step / hgks_read / hgks_destroy on one mesh."""
+
+    def __init__(self, mesh: Mesh, q0, params: hgks_params | None = None, **kw):
+        self.n_cells = mesh.n_cells
+        p = params if params is not None else make_params(**kw)
+        q0 = np.ascontiguousarray(q0, dtype=np.float64).reshape(self.n_cells, 5)
+        h = C.c_void_p()
+        _check(lib().hgks_init(mesh._h, C.byref(p), _dp(q0), C.byref(h)), "hgks_init")
+        mesh.release()
+        self._h = h
+        self.params = p
+
+    def step(self, n: int = 1, t_end: float = 0.0, dt_fixed: float = 0.0):
+        _check(lib().hgks_step(self._h, int(n), float(t_end), float(dt_fixed)), "hgks_step")
+
+    def sync(self):
+        _check(lib().hgks_sync(self._h), "hgks_sync")
+
+    def write(self, q, t: float = 0.0):
+        q = np.ascontiguousarray(q, dtype=np.float64).reshape(self.n_cells, 5)
+        _check(lib().hgks_write(self._h, _dp(q), float(t)), "hgks_write")
+
+    def read(self, out=None):
+        q = out if out is not None else np.empty((self.n_cells, 5))
+        t = C.c_double()
+        s = C.c_int64()
+        _check(lib().hgks_read(self._h, _dp(q), C.byref(t), C.byref(s)), "hgks_read")
+        return q, t.value, s.value
+
+    def stage_operator(self, dt: float):
+        L = np.empty((self.n_cells, 5))
+        dL = np.empty((self.n_cells, 5))
+        _check(lib().hgks_stage_operator(self._h, float(dt), _dp(L), _dp(dL)), "hgks_stage_operator")
+        return L, dL
+
+    def profile(self, n: int, t_end: float = 0.0, dt_fixed: float = 0.0):
+        """Average ms per step in (finalize, ghost+recon, flux, update)."""
+        ms = np.empty(4)
+        _check(lib().hgks_profile(self._h, int(n), float(t_end), float(dt_fixed), _dp(ms)), "hgks_profile")
+        return ms
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().hgks_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
