@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 # the reconstruction kernel (FP64 path), counted by ncu on the kernels as
 # built (sass dadd + dmul + 2 dfma per launch, divided by the faces or cells
 # of the launch); see profiles/flux_fp64_density12.md.  None until measured.
-FP64_FLOPS_PER_FACE_INVISCID = None
+FP64_FLOPS_PER_FACE_INVISCID = 6429  # ncu: 133.31 Mflop per launch / 20736 faces (12^3 x 6 mesh)
 FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12  # SMs x DFMA/clk x 2 flop x max SM clock
 
 

@@ -262,7 +262,7 @@ __device__ void gks_flux(const R ql[5], const R dl[3][5], const R qr[5], const R
     const R plp = pl.rho * pl.h2, prp = pr.rho * pr.h2, p0p = p0.rho * p0.h2;
     // collision time: tau = mu(T0)/p0 + C dt |p_l - p_r|/(p_l + p_r), T = p/rho
     R mu = P.mu_ref;
-    if (P.visc_exp != R(0) && mu != R(0)) mu = P.mu_ref * pow(p0.h2 * R(2) / P.T_ref, P.visc_exp);
+    if (P.visc_exp != R(0) && mu != R(0)) mu = P.mu_ref * pow(p0.h2 / P.T_ref, P.visc_exp);  // T0 = 1/(2 lam0)
     const R tau = mu / p0p + P.tau_c * dt * fabs(plp - prp) / (plp + prp);
     if (!(tau > R(0))) {
 #pragma unroll
