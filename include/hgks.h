@@ -154,6 +154,33 @@ int hgks_stage_operator(hgks_solver* s, double dt, double* L_out, double* dL_out
  * flux (both stages) and the two S2O4 updates.  Synchronises every step. */
 int hgks_profile(hgks_solver* s, int n_steps, double t_end, double dt_fixed, double* ms_out);
 
+/* Largest n_cells accepted by hgks_cfl_dt_noalloc. */
+#define HGKS_NOALLOC_MAX_CELLS 4194304
+
+/* The CFL time step of a state the caller holds on the device, computed
+ * without allocating anything: for callers that cannot call cudaMalloc at
+ * that point, such as code running while a stream is captured into a graph,
+ * hosts whose device memory belongs to another allocator, or loops that must
+ * not pay an allocation's implicit synchronisation.  The paper has no
+ * counterpart; it is the time-step reduction of hgks_step with its scratch
+ * moved into a fixed device array inside the library.
+ *   q       device pointer, [n_cells][5] conservative cell averages
+ *   hdt     device pointer, [n_cells] length scales 3|cell|/|surface|
+ *   params  host pointer; gamma, cfl, mu_ref, T_ref, visc_exp are used
+ *   dt_out  device pointer to one double: cfl min_i of the bound documented
+ *           for hgks_params.cfl (written by the GPU, stream-ordered)
+ *   stream  cudaStream_t to launch on (NULL: the legacy default stream)
+ * Scratch: a file-scope 16384-double (128 KiB) device array, one per GPU that
+ * loads the library, held until the process exits; n_cells above
+ * HGKS_NOALLOC_MAX_CELLS is rejected with HGKS_EINVAL.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress), so make
+ * that first call before any stream capture.  All calls share the array:
+ * calls that overlap on the GPU (other streams, other threads) race and must
+ * be ordered by the caller.  Calls no cudaMalloc, cudaFree or allocating
+ * library routine; returns after queueing two kernels. */
+int hgks_cfl_dt_noalloc(const double* q, const double* hdt, int64_t n_cells, const hgks_params* params,
+                        double* dt_out, void* stream);
+
 /* Free the solver, its mesh and its device memory.  NULL is ignored. */
 void hgks_destroy(hgks_solver* s);
 

@@ -101,6 +101,10 @@ void to_caller(const hgks::HostMesh& m, const double* h, int64_t stride, double*
 
 }  // namespace
 
+namespace hgks {
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace hgks
+
 extern "C" {
 
 void hgks_params_default(hgks_params* p) {

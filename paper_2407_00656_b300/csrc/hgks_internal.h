@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
 
 #include <cuda_runtime.h>
 
@@ -63,6 +64,9 @@ struct DevWork {
   void* Fs;       // [10][nf] face flux sums: F (5) then dF/dt (5) (double or float)
   Control* ctl;
 };
+
+// Message returned by hgks_last_error() on this thread.
+void set_last_error(const std::string& msg);
 
 // Per-instantiation kernel attributes; call once per solver before capture.
 void prepare_kernels(const DevMesh& m, int precision);

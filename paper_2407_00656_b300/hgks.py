@@ -86,6 +86,8 @@ def lib():
             L.hgks_read.argtypes = [vp, dp, dp, C.POINTER(C.c_int64)]
             L.hgks_stage_operator.argtypes = [vp, C.c_double, dp, dp]
             L.hgks_profile.argtypes = [vp, C.c_int, C.c_double, C.c_double, dp]
+            L.hgks_cfl_dt_noalloc.argtypes = [vp, vp, C.c_int64, C.POINTER(hgks_params), vp, vp]
+            L.hgks_cfl_dt_noalloc.restype = C.c_int
             L.hgks_destroy.argtypes = [vp]
             L.hgks_destroy.restype = None
             L.hgks_last_error.restype = C.c_char_p
@@ -123,6 +125,13 @@ def make_params(**kw) -> hgks_params:
         else:
             setattr(p, k, v)
     return p
+
+
+def cfl_dt_noalloc(q_ptr: int, hdt_ptr: int, n_cells: int, params: hgks_params, dt_ptr: int, stream: int = 0):
+    """hgks_cfl_dt_noalloc on caller-owned device buffers (raw device addresses):
+    q [n][5], hdt [n], result written to dt_ptr on the GPU."""
+    _check(lib().hgks_cfl_dt_noalloc(C.c_void_p(q_ptr), C.c_void_p(hdt_ptr), int(n_cells), C.byref(params),
+                                     C.c_void_p(dt_ptr), C.c_void_p(stream or None)), "hgks_cfl_dt_noalloc")
 
 
 class Mesh:
