@@ -216,7 +216,7 @@ int hgks_init(hgks_mesh* mesh, const hgks_params* params, const double* q0, hgks
   // carve the arena
   Carver cv{static_cast<char*>(s->arena), 0, bytes};
   hgks::DevMesh& dm = s->dm;
-  dm.nc = m.nc; dm.nf = m.nf; dm.ng = m.ng; dm.nce = m.nc + m.ng;
+  dm.nc = m.nc; dm.nf = m.nf; dm.ng = m.ng; dm.nce = m.nc + m.ng; dm.ncp = m.ncp;
   dm.K = m.K; dm.M = m.M; dm.KM = m.KM; dm.G = m.G; dm.nfc = m.nfc;
   std::vector<double> volinv(m.nc);
   for (int64_t c = 0; c < m.nc; ++c) volinv[c] = 1.0 / m.vol[c];
@@ -227,9 +227,9 @@ int hgks_init(hgks_mesh* mesh, const hgks_params* params, const double* q0, hgks
   cv.take<double>(3 * m.nc);  // centroids are baked into the face offsets; slot kept for the size formula
   double* p_mom = cv.take<double>(6 * m.nc);
   int32_t* p_sten = cv.take<int32_t>((int64_t)m.K * m.nc);
-  double* p_pinv0 = cv.take<double>((int64_t)9 * m.K * m.nc);
-  uint8_t* p_subidx = cv.take<uint8_t>((int64_t)m.M * m.KM * m.nc);
-  double* p_pinvm = cv.take<double>((int64_t)m.M * 3 * m.KM * m.nc);
+  double* p_pinv0 = cv.take<double>((int64_t)9 * m.K * m.ncp);
+  uint8_t* p_subidx = cv.take<uint8_t>((int64_t)m.M * m.KM * m.ncp);
+  double* p_pinvm = cv.take<double>((int64_t)m.M * 3 * m.KM * m.ncp);
   int32_t* p_cface = cv.take<int32_t>((int64_t)m.nfc * m.nc);
   int32_t* p_gsrc = cv.take<int32_t>(m.ng);
   int32_t* p_gtag = cv.take<int32_t>(m.ng);
@@ -352,6 +352,7 @@ int hgks_sync(hgks_solver* s) {
   HGKS_CUDA(cudaGetLastError(), "synchronising");
   hgks::Control c;
   HGKS_CUDA(cudaMemcpy(&c, s->dw.ctl, sizeof c, cudaMemcpyDeviceToHost), "reading the control block");
+  if (c.flags & hgks::FLAG_TIMEOUT) return fail(HGKS_ETIMEOUT, "a bounded wait for staged copies ran out");
   if (c.flags & hgks::FLAG_NONFINITE) return fail(HGKS_ENONFINITE, "a step produced a non-finite cell average");
   return HGKS_OK;
 }
@@ -369,6 +370,7 @@ int hgks_read(hgks_solver* s, double* q_out, double* t_out, int64_t* steps_out) 
   }
   if (t_out) *t_out = c.t;
   if (steps_out) *steps_out = c.steps;
+  if (c.flags & hgks::FLAG_TIMEOUT) return fail(HGKS_ETIMEOUT, "a bounded wait for staged copies ran out");
   if (c.flags & hgks::FLAG_NONFINITE) return fail(HGKS_ENONFINITE, "a step produced a non-finite cell average");
   return HGKS_OK;
 }

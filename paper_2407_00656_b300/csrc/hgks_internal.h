@@ -12,15 +12,16 @@ namespace hgks {
 // Read-only mesh arrays in device memory (layouts as in mesh_builder.h).
 struct DevMesh {
   int64_t nc, nf, ng, nce;  // cells, faces, ghosts, cells + ghosts
+  int64_t ncp;              // row pitch of pinv0, subidx, pinvm (nc rounded up to 32)
   int K, M, KM, G, nfc;
   const double* volinv;   // [nc] 1/|cell|
   const double* hdt;      // [nc]
   const double* hinv;     // [nc]
   const double* mom;      // [6][nc] scaled central second moments
   const int32_t* sten;    // [K][nc]
-  const double* pinv0;    // [9K][nc]
-  const uint8_t* subidx;  // [M*KM][nc]
-  const double* pinvm;    // [M*3*KM][nc]
+  const double* pinv0;    // [9K][ncp]
+  const uint8_t* subidx;  // [M*KM][ncp]
+  const double* pinvm;    // [M*3*KM][ncp]
   const int32_t* cface;   // [nfc][nc]
   const int32_t* gsrc;    // [ng]
   const int32_t* gtag;    // [ng]
@@ -52,7 +53,7 @@ struct Control {
   int pad;
 };
 
-enum { FLAG_NONFINITE = 1 };
+enum { FLAG_NONFINITE = 1, FLAG_TIMEOUT = 2 };
 
 // Work arrays of one solver.
 struct DevWork {

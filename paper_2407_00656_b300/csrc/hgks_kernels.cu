@@ -34,6 +34,27 @@ __device__ __forceinline__ void sfor(F&& f) {
   }
 }
 
+// binary64 -> Real.  For binary32 the conversion is done with integer
+// operations on the IEEE-754 fields (round to nearest, ties away from zero),
+// which keeps it off the FP64 pipe; valid for |x| in [2^-126, 2^128), smaller
+// magnitudes flush to a signed zero.  Used for the stored binary64 geometry and
+// pseudo-inverses read by the mixed-precision kernels.
+template <typename Real>
+__device__ __forceinline__ Real cvt(double x);
+template <>
+__device__ __forceinline__ double cvt<double>(double x) {
+  return x;
+}
+template <>
+__device__ __forceinline__ float cvt<float>(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  const unsigned sign = hi & 0x80000000u;
+  const unsigned r = (sign | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29)) + ((lo >> 28) & 1u);
+  return __uint_as_float(e < 897u ? sign : r);
+}
+
 // --------------------------------------------------------------------------
 // Maxwellian moments.  Mom holds normalised one-dimensional moments <u^k>,
 // <v^k>, <w^k> and <(xi^2)^k> of one Maxwellian (u possibly on a half-line).
@@ -80,18 +101,19 @@ struct Prim {
   R rho, U, V, W, lam, h2;  // h2 = 1/(2 lam)
 };
 
+// kq = (K+3)/4: rho E = rho |U|^2/2 + kq rho / lam, so lam = kq rho / eint and
+// 1/(2 lam) = eint / (2 kq rho); two reciprocals per state.
 template <typename R>
-__device__ __forceinline__ Prim<R> prim_of(const R q[5], R Kint) {
+__device__ __forceinline__ Prim<R> prim_of(const R q[5], R kq, R kqi) {
   Prim<R> p;
   p.rho = q[0];
   const R ri = R(1) / q[0];
   p.U = q[1] * ri;
   p.V = q[2] * ri;
   p.W = q[3] * ri;
-  // rho E = rho |U|^2 / 2 + (K+3) rho / (4 lam)
   const R eint = q[4] - R(0.5) * (q[1] * p.U + q[2] * p.V + q[3] * p.W);
-  p.h2 = R(2) * eint / ((Kint + R(3)) * q[0]);
-  p.lam = R(0.5) / p.h2;
+  p.lam = kq * q[0] / eint;
+  p.h2 = R(0.5) * kqi * eint * ri;
   return p;
 }
 
@@ -102,9 +124,9 @@ __device__ __forceinline__ void moments(const Prim<R>& p, int half, R Kint, Mom<
     M.u[0] = R(1);
     M.u[1] = p.U;
   } else {
-    const R sl = sqrt(p.lam);
-    const R s = R(half) * sl * p.U;
-    const R e = exp(-p.lam * p.U * p.U) * R(0.28209479177387814) / sl;  // exp(-lam U^2)/(2 sqrt(pi lam))
+    const R rs = rsqrt(p.lam);
+    const R s = R(half) * p.lam * rs * p.U;  // sqrt(lam) U
+    const R e = exp(-p.lam * p.U * p.U) * R(0.28209479177387814) * rs;  // exp(-lam U^2)/(2 sqrt(pi lam))
     M.u[0] = R(0.5) * erfc(-s);
     M.u[1] = p.U * M.u[0] + R(half) * e;
   }
@@ -124,12 +146,12 @@ __device__ __forceinline__ void moments(const Prim<R>& p, int half, R Kint, Mom<
 // 2.1), in closed form: returns rho * a for the polynomial a(psi) with
 // rho <a psi> = dq under the Maxwellian p.
 template <typename R>
-__device__ __forceinline__ void micro_slope_rho(const Prim<R>& p, R Kint, const R dq[5], R a[5]) {
+__device__ __forceinline__ void micro_slope_rho(const Prim<R>& p, R kq, R kqi, const R dq[5], R a[5]) {
   const R b0 = dq[0];
   const R r1 = dq[1] - p.U * b0, r2 = dq[2] - p.V * b0, r3 = dq[3] - p.W * b0;
-  const R E = p.U * p.U + p.V * p.V + p.W * p.W + (Kint + R(3)) * p.h2;
+  const R E = p.U * p.U + p.V * p.V + p.W * p.W + R(4) * kq * p.h2;  // |U|^2 + (K+3)/(2 lam)
   const R r4 = R(2) * dq[4] - E * b0;
-  a[4] = R(4) * p.lam * p.lam / (Kint + R(3)) * (r4 - R(2) * (p.U * r1 + p.V * r2 + p.W * r3));
+  a[4] = p.lam * p.lam * kqi * (r4 - R(2) * (p.U * r1 + p.V * r2 + p.W * r3));  // 4 lam^2/(K+3)
   const R tl = R(2) * p.lam;
   a[1] = tl * r1 - p.U * a[4];
   a[2] = tl * r2 - p.V * a[4];
@@ -169,7 +191,7 @@ __device__ __forceinline__ void euler_jv(const EState<R>& s, const R d[5], R o[5
 
 template <typename R>
 struct FluxParams {
-  R gamma, Kint, mu_ref, T_ref, visc_exp, Pr, tau_c;
+  R gamma, Kint, kq, kqi, mu_ref, T_ref, visc_exp, Pr, tau_c;  // kq = (K+3)/4, kqi = 1/kq
 };
 
 // <u psi_i P> for P = a.u (a_j micro-slopes along x, y, z, rho-weighted),
@@ -198,7 +220,7 @@ template <typename R, bool VISC>
 __device__ void gks_flux(const R ql[5], const R dl[3][5], const R qr[5], const R dr[3][5], R dt,
                          const FluxParams<R>& P, R F[5], R dF[5]) {
   const R K = P.Kint;
-  const Prim<R> pl = prim_of(ql, K), pr = prim_of(qr, K);
+  const Prim<R> pl = prim_of(ql, P.kq, P.kqi), pr = prim_of(qr, P.kq, P.kqi);
   constexpr int NU = VISC ? 7 : 5;
   Mom<R> Ml, Mr;
   moments<NU>(pl, +1, K, Ml);
@@ -226,8 +248,8 @@ __device__ void gks_flux(const R ql[5], const R dl[3][5], const R qr[5], const R
   R al[3][5], ar[3][5];
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    micro_slope_rho(pl, K, dl[j], al[j]);  // rho_l a^l_j
-    micro_slope_rho(pr, K, dr[j], ar[j]);
+    micro_slope_rho(pl, P.kq, P.kqi, dl[j], al[j]);  // rho_l a^l_j
+    micro_slope_rho(pr, P.kq, P.kqi, dr[j], ar[j]);
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
       R s = R(0);
@@ -258,7 +280,7 @@ __device__ void gks_flux(const R ql[5], const R dl[3][5], const R qr[5], const R
     for (int i = 0; i < 5; ++i) { F[i] = Fe[i]; dF[i] = Ye[i]; }
     return;
   } else {
-    const Prim<R> p0 = prim_of(q0, K);
+    const Prim<R> p0 = prim_of(q0, P.kq, P.kqi);
     const R plp = pl.rho * pl.h2, prp = pr.rho * pr.h2, p0p = p0.rho * p0.h2;
     // collision time: tau = mu(T0)/p0 + C dt |p_l - p_r|/(p_l + p_r), T = p/rho
     R mu = P.mu_ref;
@@ -272,7 +294,7 @@ __device__ void gks_flux(const R ql[5], const R dl[3][5], const R qr[5], const R
     // rho0 abar_j and rho0 Abar
     R ab[3][5];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) micro_slope_rho(p0, K, dq0[j], ab[j]);
+    for (int j = 0; j < 3; ++j) micro_slope_rho(p0, P.kq, P.kqi, dq0[j], ab[j]);
     Mom<R> M0;
     moments<7>(p0, 0, K, M0);
     R X0[5];
@@ -286,14 +308,14 @@ __device__ void gks_flux(const R ql[5], const R dl[3][5], const R qr[5], const R
       euler_jv<2>(sl, dl[2], s2);
 #pragma unroll
       for (int i = 0; i < 5; ++i) tmp[i] = -(tmp[i] + s1[i] + s2[i]);
-      micro_slope_rho(pl, K, tmp, Al);
+      micro_slope_rho(pl, P.kq, P.kqi, tmp, Al);
       const EState<R> sr = estate(qr, P.gamma);
       euler_jv<0>(sr, dr[0], tmp);
       euler_jv<1>(sr, dr[1], s1);
       euler_jv<2>(sr, dr[2], s2);
 #pragma unroll
       for (int i = 0; i < 5; ++i) tmp[i] = -(tmp[i] + s1[i] + s2[i]);
-      micro_slope_rho(pr, K, tmp, Ar);
+      micro_slope_rho(pr, P.kq, P.kqi, tmp, Ar);
     }
     R Xl[5], Xr[5], Nk[5], Yk[5];
     flux_of_slope(Ml, al, Xl);
@@ -500,111 +522,208 @@ __global__ void __launch_bounds__(kBlock) k_ghost(DevMesh m, DevParams P, double
 // WENO reconstruction, one thread per cell.  Output coef[(v*10+j)*nc + c]:
 // the combined polynomial P(x) = q + g.d + sum k_ab d_a d_b, d = x - centroid,
 // j = 0: q, 1-3: g, 4-9: k_xx k_yy k_zz k_xy k_yz k_zx.
-// The stencil differences live in dynamic shared memory, sdq[(k*5+v)*kRecon + t],
-// because the sub-stencil members are addressed by per-cell indices.
-constexpr int kRecon = 64;
+// Smoothness indicators, WENO-Z weights and the combined polynomial of one
+// variable (Section 2.3, Eq. weno), written to out[j*nc], j = 0..9.
+template <typename Real, int M>
+__device__ __forceinline__ void recon_finish(const Real a[9], const Real b[M][3], Real qv, const Real mi[6], Real hi,
+                                             Real glin, Real g0, Real eps, Real* __restrict__ out, int64_t nc) {
+  // smoothness indicators (scaled coordinates; the |cell| powers cancel):
+  // beta_0 = sum_a (a_a^2 + H_a.Mi.H_a) + sum_{|l|=2} (d^l P0)^2, beta_m = |b_m|^2
+  const Real H[3][3] = {{Real(2) * a[3], a[6], a[8]}, {a[6], Real(2) * a[4], a[7]}, {a[8], a[7], Real(2) * a[5]}};
+  Real beta0 = Real(0);
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    const Real h0 = H[x][0], h1 = H[x][1], h2 = H[x][2];
+    const Real quad = h0 * (mi[0] * h0 + mi[3] * h1 + mi[5] * h2) + h1 * (mi[3] * h0 + mi[1] * h1 + mi[4] * h2) +
+                      h2 * (mi[5] * h0 + mi[4] * h1 + mi[2] * h2);
+    beta0 += a[x] * a[x] + quad;
+  }
+  beta0 += H[0][0] * H[0][0] + H[1][1] * H[1][1] + H[2][2] * H[2][2] + a[6] * a[6] + a[7] * a[7] + a[8] * a[8];
+  Real beta[M];
+  Real tz = Real(0);
+#pragma unroll
+  for (int s = 0; s < M; ++s) {
+    beta[s] = b[s][0] * b[s][0] + b[s][1] * b[s][1] + b[s][2] * b[s][2];
+    tz += fabs(beta0 - beta[s]);
+  }
+  tz *= Real(1) / Real(M);
+  // WENO-Z type weights
+  Real w0 = g0 * (Real(1) + tz / (beta0 + eps));
+  Real w[M];
+  Real wsum = w0;
+#pragma unroll
+  for (int s = 0; s < M; ++s) {
+    w[s] = glin * (Real(1) + tz / (beta[s] + eps));
+    wsum += w[s];
+  }
+  const Real winv = Real(1) / wsum;
+  const Real c0 = w0 * winv / g0;  // wbar_0 / gamma_0
+  Real lin[3] = {c0 * a[0], c0 * a[1], c0 * a[2]};
+#pragma unroll
+  for (int s = 0; s < M; ++s) {
+    const Real cm = w[s] * winv - c0 * glin;  // wbar_m - wbar_0 gamma_m / gamma_0
+#pragma unroll
+    for (int d = 0; d < 3; ++d) lin[d] += cm * b[s][d];
+  }
+  Real quad[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) quad[q] = c0 * a[3 + q];
+  // to physical units about the centroid; the zero-mean basis shifts the constant
+  Real q0 = qv;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) q0 -= quad[q] * mi[q];
+  out[0] = q0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) out[(1 + d) * nc] = lin[d] * hi;
+  const Real hi2 = hi * hi;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) out[(4 + q) * nc] = quad[q] * hi2;
+}
+
+// --------------------------------------------------------------------------
+// Bulk asynchronous copies (TMA engine) into shared memory, completed on an
+// mbarrier.  Addresses and sizes are multiples of 16 bytes by construction
+// (rows of 32 cells with a 32-cell row pitch).
+// --------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase of bar with the given parity to complete: false
+// after about 2^31 clock cycles (~1 s).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > (1LL << 31)) return false;
+  return true;
+}
+
+// WENO reconstruction, one block per kRC = 32 consecutive cells with one warp
+// per conservative variable (5 warps).  Warp 0 stages the block's rows of the
+// pseudo-inverses (9K quadratic rows, then 3*KM rows per sub-stencil; 32
+// cells of a row are 256 contiguous bytes) and the sub-stencil positions in
+// shared memory with bulk asynchronous copies, while every warp gathers its
+// variable's stencil differences; the rows are then reduced against them.
+// Output coef[(v*10+j)*nc + c]: P(x) = q + g.d + sum k_ab d_a d_b with
+// d = x - centroid; j = 0: q, 1-3: g, 4-9: k_xx k_yy k_zz k_xy k_yz k_zx.
+constexpr int kRC = 32;
+constexpr int kRThreads = 5 * kRC;
+
+template <typename Real, int K, int M, int KM>
+struct ReconSmem {
+  static constexpr int kRows = 9 * K + M * 3 * KM;
+  static constexpr size_t tile = sizeof(double) * kRows * kRC;   // staged rows (binary64)
+  static constexpr size_t sub = (size_t)M * KM * kRC;            // staged positions
+  static constexpr size_t dq = sizeof(Real) * 5 * K * kRC;       // stencil differences
+  static constexpr size_t bytes = tile + sub + dq;
+};
 
 template <typename Real, typename QT, int K, int M, int KM>
-__global__ void __launch_bounds__(kRecon) k_recon(DevMesh m, DevParams P, const QT* __restrict__ Q,
-                                                  Real* __restrict__ coef, const Control* __restrict__ ctl) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Real* sdq = reinterpret_cast<Real*>(smem_raw);
-  const int64_t nc = m.nc;
-  const int64_t c = (int64_t)blockIdx.x * kRecon + threadIdx.x;
-  if (c >= nc || ctl->dt == 0.0) return;
-  const int t = threadIdx.x;
-  Real qi[5];
+__global__ void __launch_bounds__(kRThreads) k_recon(DevMesh m, DevParams P, const QT* __restrict__ Q,
+                                                     Real* __restrict__ coef, Control* __restrict__ ctl) {
+  using S = ReconSmem<Real, K, M, KM>;
+  constexpr int kRows = S::kRows;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  double* tile = reinterpret_cast<double*>(smem_raw);                // [kRows][kRC]
+  uint8_t* ssub = smem_raw + S::tile;                                // [M*KM][kRC]
+  Real* sdq = reinterpret_cast<Real*>(smem_raw + S::tile + S::sub);  // [5][K][kRC]
+  __shared__ __align__(8) uint64_t bar;
+  if (ctl->dt == 0.0) return;  // uniform over the grid
+  const int64_t nc = m.nc, ncp = m.ncp;
+  const int lane = threadIdx.x & 31, v = threadIdx.x >> 5;
+  const int64_t c0 = (int64_t)blockIdx.x * kRC;
+  const int64_t c = c0 + lane;
+  const bool valid = c < nc;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (v == 0) {
+    if (lane == 0) mbar_expect_tx(&bar, (uint32_t)(S::tile + S::sub));
+    __syncwarp();
+    for (int r = lane; r < kRows; r += 32) {
+      const double* src = r < 9 * K ? m.pinv0 + (int64_t)r * ncp + c0 : m.pinvm + (int64_t)(r - 9 * K) * ncp + c0;
+      bulk_g2s(tile + r * kRC, src, kRC * sizeof(double), &bar);
+    }
+    for (int r = lane; r < M * KM; r += 32) bulk_g2s(ssub + r * kRC, m.subidx + (int64_t)r * ncp + c0, kRC, &bar);
+  }
+  // this warp's variable: stencil differences (overlaps the staging)
+  Real qv = Real(0);
+  if (valid) {
+    qv = (Real)Q[v * m.nce + c];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) qi[v] = (Real)Q[v * m.nce + c];
+    for (int k = 0; k < K; ++k) {
+      const int64_t j = m.sten[(int64_t)k * nc + c];
+      sdq[(v * K + k) * kRC + lane] = (Real)Q[v * m.nce + j] - qv;
+    }
+  }
+  const bool ok = __syncthreads_and(mbar_wait_bounded(&bar, 0));
+  if (!ok) {
+    if (threadIdx.x == 0) atomicOr(&ctl->flags, FLAG_TIMEOUT);
+    mbar_wait_bounded(&bar, 0);  // copies in flight: a second bounded wait before leaving
+    return;
+  }
+  if constexpr (sizeof(Real) == 4) {
+    // binary32: convert the staged rows in place (low word of each slot), once
+    float* tf = reinterpret_cast<float*>(tile);
+    for (int e = threadIdx.x; e < kRows * kRC; e += kRThreads) tf[2 * e] = cvt<float>(tile[e]);
+    __syncthreads();
+  }
+  if (!valid) return;
+  auto row = [&](int r) -> Real {
+    if constexpr (sizeof(Real) == 4) return reinterpret_cast<const float*>(tile)[2 * (r * kRC + lane)];
+    else return tile[r * kRC + lane];
+  };
+  Real dq[K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const int64_t j = m.sten[k * nc + c];
+  for (int k = 0; k < K; ++k) dq[k] = sdq[(v * K + k) * kRC + lane];
+  // least-squares polynomials
+  Real a[9];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) sdq[(k * 5 + v) * kRecon + t] = (Real)Q[v * m.nce + j] - qi[v];
+  for (int d = 0; d < 9; ++d) {
+    Real sacc = Real(0);
+#pragma unroll
+    for (int k = 0; k < K; ++k) sacc += row(d * K + k) * dq[k];
+    a[d] = sacc;
+  }
+  Real b[M][3];
+#pragma unroll
+  for (int s = 0; s < M; ++s) {
+    Real x[KM];
+#pragma unroll
+    for (int r = 0; r < KM; ++r) x[r] = sdq[(v * K + ssub[(s * KM + r) * kRC + lane]) * kRC + lane];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      Real acc = Real(0);
+#pragma unroll
+      for (int r = 0; r < KM; ++r) acc += row(9 * K + (s * 3 + d) * KM + r) * x[r];
+      b[s][d] = acc;
+    }
   }
   Real mi[6];
 #pragma unroll
-  for (int q = 0; q < 6; ++q) mi[q] = (Real)m.mom[q * nc + c];
-  const Real hi = (Real)m.hinv[c];
+  for (int q = 0; q < 6; ++q) mi[q] = cvt<Real>(m.mom[q * nc + c]);
+  const Real hi = cvt<Real>(m.hinv[c]);
   const Real glin = (Real)P.glin, g0 = Real(1) - Real(M) * glin, eps = (Real)P.eps;
-  uint8_t sidx[M * KM];
-#pragma unroll
-  for (int r = 0; r < M * KM; ++r) sidx[r] = m.subidx[r * nc + c];
-
-#pragma unroll 1
-  for (int v = 0; v < 5; ++v) {
-    Real a[9];
-#pragma unroll
-    for (int d = 0; d < 9; ++d) {
-      Real s = Real(0);
-#pragma unroll
-      for (int k = 0; k < K; ++k) s += (Real)m.pinv0[(d * K + k) * nc + c] * sdq[(k * 5 + v) * kRecon + t];
-      a[d] = s;
-    }
-    Real b[M][3];
-#pragma unroll
-    for (int s = 0; s < M; ++s)
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        Real acc = Real(0);
-#pragma unroll
-        for (int r = 0; r < KM; ++r)
-          acc += (Real)m.pinvm[((s * 3 + d) * KM + r) * nc + c] * sdq[(sidx[s * KM + r] * 5 + v) * kRecon + t];
-        b[s][d] = acc;
-      }
-    // smoothness indicators (scaled coordinates; the |cell| powers cancel):
-    // beta_0 = sum_a (a_a^2 + H_a.Mi.H_a) + sum_{|l|=2} (d^l P0)^2, beta_m = |b_m|^2
-    const Real H[3][3] = {{Real(2) * a[3], a[6], a[8]}, {a[6], Real(2) * a[4], a[7]}, {a[8], a[7], Real(2) * a[5]}};
-    Real beta0 = Real(0);
-#pragma unroll
-    for (int x = 0; x < 3; ++x) {
-      const Real h0 = H[x][0], h1 = H[x][1], h2 = H[x][2];
-      const Real quad = h0 * (mi[0] * h0 + mi[3] * h1 + mi[5] * h2) + h1 * (mi[3] * h0 + mi[1] * h1 + mi[4] * h2) +
-                        h2 * (mi[5] * h0 + mi[4] * h1 + mi[2] * h2);
-      beta0 += a[x] * a[x] + quad;
-    }
-    beta0 += H[0][0] * H[0][0] + H[1][1] * H[1][1] + H[2][2] * H[2][2] + a[6] * a[6] + a[7] * a[7] + a[8] * a[8];
-    Real beta[M];
-    Real tz = Real(0);
-#pragma unroll
-    for (int s = 0; s < M; ++s) {
-      beta[s] = b[s][0] * b[s][0] + b[s][1] * b[s][1] + b[s][2] * b[s][2];
-      tz += fabs(beta0 - beta[s]);
-    }
-    tz *= Real(1) / Real(M);
-    // WENO-Z type weights
-    Real w0 = g0 * (Real(1) + tz / (beta0 + eps));
-    Real w[M];
-    Real wsum = w0;
-#pragma unroll
-    for (int s = 0; s < M; ++s) {
-      w[s] = glin * (Real(1) + tz / (beta[s] + eps));
-      wsum += w[s];
-    }
-    const Real winv = Real(1) / wsum;
-    const Real c0 = w0 * winv / g0;  // wbar_0 / gamma_0
-    Real lin[3] = {c0 * a[0], c0 * a[1], c0 * a[2]};
-#pragma unroll
-    for (int s = 0; s < M; ++s) {
-      const Real cm = w[s] * winv - c0 * glin;  // wbar_m - wbar_0 gamma_m / gamma_0
-#pragma unroll
-      for (int d = 0; d < 3; ++d) lin[d] += cm * b[s][d];
-    }
-    Real quad[6];
-#pragma unroll
-    for (int q = 0; q < 6; ++q) quad[q] = c0 * a[3 + q];
-    // to physical units about the centroid; the zero-mean basis shifts the constant
-    Real q0 = qi[v];
-#pragma unroll
-    for (int q = 0; q < 6; ++q) q0 -= quad[q] * mi[q];
-    Real* out = coef + (int64_t)v * 10 * nc + c;
-    out[0] = q0;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) out[(1 + d) * nc] = lin[d] * hi;
-    const Real hi2 = hi * hi;
-#pragma unroll
-    for (int q = 0; q < 6; ++q) out[(4 + q) * nc] = quad[q] * hi2;
-  }
+  recon_finish<Real, M>(a, b, qv, mi, hi, glin, g0, eps, coef + (int64_t)v * 10 * nc + c, nc);
 }
 
 // Point value and gradient of the combined polynomial of cell c at offset d.
@@ -640,6 +759,8 @@ __global__ void __launch_bounds__(kBlock) k_flux(DevMesh m, DevParams P, const R
   FluxParams<Real> FP;
   FP.gamma = (Real)P.gamma;
   FP.Kint = (Real)P.Kint;
+  FP.kq = (Real)(0.25 * (P.Kint + 3.0));
+  FP.kqi = (Real)(4.0 / (P.Kint + 3.0));
   FP.mu_ref = (Real)P.mu_ref;
   FP.T_ref = (Real)P.T_ref;
   FP.visc_exp = (Real)P.visc_exp;
@@ -648,17 +769,24 @@ __global__ void __launch_bounds__(kBlock) k_flux(DevMesh m, DevParams P, const R
   const int64_t own = m.fown[f];
   const int nbr = m.fnbr[f];
   Real Fa[5] = {0, 0, 0, 0, 0}, Da[5] = {0, 0, 0, 0, 0};
+  // planar triangles share one normal and frame; bilinear quads have one per point
+  Real n[3], t1[3], t2[3];
+  if constexpr (G == 3) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) n[a] = cvt<Real>(m.fn[a * nf + f]);
+    frame(n, t1, t2);
+  }
 #pragma unroll 1
   for (int g = 0; g < G; ++g) {
-    Real n[3], d[3];
+    Real d[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      n[a] = (Real)m.fn[(g * 3 + a) * nf + f];
-      d[a] = (Real)m.fdl[(g * 3 + a) * nf + f];
+    for (int a = 0; a < 3; ++a) d[a] = cvt<Real>(m.fdl[(g * 3 + a) * nf + f]);
+    if constexpr (G != 3) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) n[a] = cvt<Real>(m.fn[(g * 3 + a) * nf + f]);
+      frame(n, t1, t2);
     }
-    const Real wgt = (Real)m.fw[g * nf + f];
-    Real t1[3], t2[3];
-    frame(n, t1, t2);
+    const Real wgt = cvt<Real>(m.fw[g * nf + f]);
     Real qv[5], gr[5][3];
     eval_poly(coef, nc, own, d, qv, gr);
     // local frame: rotate momentum, take derivatives along n, t1, t2
@@ -686,7 +814,7 @@ __global__ void __launch_bounds__(kBlock) k_flux(DevMesh m, DevParams P, const R
     local(qv, gr, ql, dl);
     if (nbr >= 0) {
 #pragma unroll
-      for (int a = 0; a < 3; ++a) d[a] = (Real)m.fdr[(g * 3 + a) * nf + f];
+      for (int a = 0; a < 3; ++a) d[a] = cvt<Real>(m.fdr[(g * 3 + a) * nf + f]);
       eval_poly(coef, nc, (int64_t)nbr, d, qv, gr);
       local(qv, gr, qr, dr);
     } else if (nbr == -3) {
@@ -733,25 +861,26 @@ __global__ void __launch_bounds__(kBlock) k_flux(DevMesh m, DevParams P, const R
   }
 }
 
-// Gather of the face fluxes into L and dL/dt of cell c (Eq. finite).
+// Gather of the face fluxes into L and dL/dt of cell c (Eq. finite).  The
+// face sum runs in the flux precision; L and dL enter the S2O4 sums in binary64.
 template <typename Real, int NFC>
 __device__ __forceinline__ void gather(const DevMesh& m, const Real* __restrict__ Fs, int64_t c, double L[5],
                                        double dL[5]) {
-  for (int v = 0; v < 5; ++v) L[v] = dL[v] = 0.0;
+  Real a[5] = {0, 0, 0, 0, 0}, b[5] = {0, 0, 0, 0, 0};
 #pragma unroll
   for (int p = 0; p < NFC; ++p) {
     const int32_t e = m.cface[p * m.nc + c];
     const int64_t f = e >> 1;
-    const double sg = (e & 1) ? -1.0 : 1.0;
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      L[v] += sg * (double)Fs[v * m.nf + f];
-      dL[v] += sg * (double)Fs[(5 + v) * m.nf + f];
+      const Real x = Fs[v * m.nf + f], y = Fs[(5 + v) * m.nf + f];
+      a[v] += (e & 1) ? -x : x;
+      b[v] += (e & 1) ? -y : y;
     }
   }
   const double vi = -m.volinv[c];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) { L[v] *= vi; dL[v] *= vi; }
+  for (int v = 0; v < 5; ++v) { L[v] = (double)a[v] * vi; dL[v] = (double)b[v] * vi; }
 }
 
 // Stage 1: Q* = Q + dt/2 L + dt^2/8 dL;  R = Q + dt L + dt^2/6 dL.
@@ -822,27 +951,22 @@ __global__ void k_operator(DevMesh m, const Real* __restrict__ Fs, double* __res
 
 inline unsigned blocks(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
-// Stencil shapes compiled in: tets (K up to 16, 4 sub-stencils of 6),
-// hexes (K up to 24, 8 octants of 3).
-// prep = true only opts the instantiation in to its dynamic shared memory size
-// (above 48 KB for FP64 hexahedra); this happens at solver creation, before
-// any stream capture.
 template <typename Real, typename QT, int K, int M, int KM>
-void recon_launch(const DevMesh& m, const DevParams& p, const QT* Q, Real* coef, const Control* ctl, cudaStream_t s,
+void recon_launch(const DevMesh& m, const DevParams& p, const QT* Q, Real* coef, Control* ctl, cudaStream_t s,
                   bool prep) {
-  const size_t smem = sizeof(Real) * K * 5 * kRecon;
+  const size_t smem = ReconSmem<Real, K, M, KM>::bytes;
   if (prep) {
     cudaFuncSetAttribute(k_recon<Real, QT, K, M, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return;
   }
-  const unsigned nb = (unsigned)((m.nc + kRecon - 1) / kRecon);
-  k_recon<Real, QT, K, M, KM><<<nb, kRecon, smem, s>>>(m, p, Q, coef, ctl);
+  const unsigned nb = (unsigned)((m.nc + kRC - 1) / kRC);
+  k_recon<Real, QT, K, M, KM><<<nb, kRThreads, smem, s>>>(m, p, Q, coef, ctl);
 }
 
 // Stencil shapes compiled in: tetrahedra with 12..16 members and 4 sub-stencils
 // of up to 6; hexahedra with 18..24 members and 8 octants of 3.
 template <typename Real, typename QT, int M, int KM>
-void recon_dispatch(const DevMesh& m, const DevParams& p, const QT* Q, Real* coef, const Control* ctl, cudaStream_t s,
+void recon_dispatch(const DevMesh& m, const DevParams& p, const QT* Q, Real* coef, Control* ctl, cudaStream_t s,
                     bool prep) {
   switch (m.K) {
     case 12: recon_launch<Real, QT, 12, M, KM>(m, p, Q, coef, ctl, s, prep); break;
@@ -854,7 +978,7 @@ void recon_dispatch(const DevMesh& m, const DevParams& p, const QT* Q, Real* coe
   }
 }
 template <typename Real, typename QT>
-void recon_hex(const DevMesh& m, const DevParams& p, const QT* Q, Real* coef, const Control* ctl, cudaStream_t s,
+void recon_hex(const DevMesh& m, const DevParams& p, const QT* Q, Real* coef, Control* ctl, cudaStream_t s,
                bool prep) {
   switch (m.K) {
     case 18: recon_launch<Real, QT, 18, 8, 3>(m, p, Q, coef, ctl, s, prep); break;
@@ -874,7 +998,7 @@ bool stencil_supported(int nfc, int K) {
 namespace {
 
 template <typename Real, typename QT>
-void recon_any(const DevMesh& m, const DevParams& p, const QT* Q, Real* coef, const Control* ctl, cudaStream_t s,
+void recon_any(const DevMesh& m, const DevParams& p, const QT* Q, Real* coef, Control* ctl, cudaStream_t s,
                bool prep = false) {
   if (m.M == 4) recon_dispatch<Real, QT, 4, 6>(m, p, Q, coef, ctl, s, prep);
   else recon_hex<Real, QT>(m, p, Q, coef, ctl, s, prep);
@@ -902,7 +1026,7 @@ void stage_pair(const DevMesh& m, const DevParams& p, const DevWork& w, bool mix
   auto mark = [&](int i) { if (ev) cudaEventRecord(ev->ev[i], s); };
   // stage 1 on Q^n
   if (m.ng) k_ghost<<<blocks(m.ng), kBlock, 0, s>>>(m, p, w.Q, Qf, w.ctl);
-  if (mixed) recon_any<Real, float>(m, p, w.Qf, coef, w.ctl, s);
+  if constexpr (std::is_same_v<Real, float>) recon_any<Real, float>(m, p, w.Qf, coef, w.ctl, s);
   else recon_any<Real, double>(m, p, w.Q, coef, w.ctl, s);
   mark(2);
   flux_any<Real>(m, p, coef, Fs, w.ctl, s);
@@ -912,7 +1036,7 @@ void stage_pair(const DevMesh& m, const DevParams& p, const DevWork& w, bool mix
   mark(4);
   // stage 2 on Q*
   if (m.ng) k_ghost<<<blocks(m.ng), kBlock, 0, s>>>(m, p, w.Qs, Qf, w.ctl);
-  if (mixed) recon_any<Real, float>(m, p, w.Qf, coef, w.ctl, s);
+  if constexpr (std::is_same_v<Real, float>) recon_any<Real, float>(m, p, w.Qf, coef, w.ctl, s);
   else recon_any<Real, double>(m, p, w.Qs, coef, w.ctl, s);
   mark(5);
   flux_any<Real>(m, p, coef, Fs, w.ctl, s);

@@ -566,9 +566,11 @@ int build_host_mesh(const hgks_mesh_desc& d, HostMesh& m, std::string& err) {
   m.K = K;
   const int M = m.M, KM = m.KM;
   m.sten.assign((int64_t)K * nc, 0);
-  m.pinv0.assign((int64_t)9 * K * nc, 0.0);
-  m.subidx.assign((int64_t)M * KM * nc, 0);
-  m.pinvm.assign((int64_t)M * 3 * KM * nc, 0.0);
+  const int64_t ncp = (nc + 31) / 32 * 32;
+  m.ncp = ncp;
+  m.pinv0.assign((int64_t)9 * K * ncp, 0.0);
+  m.subidx.assign((int64_t)M * KM * ncp, 0);
+  m.pinvm.assign((int64_t)M * 3 * KM * ncp, 0.0);
   int64_t fail = -1;
   const char* fail_msg = "";
 #pragma omp parallel for schedule(dynamic, 256)
@@ -640,8 +642,8 @@ int build_host_mesh(const hgks_mesh_desc& d, HostMesh& m, std::string& err) {
       }
       if (!ok || !mgs2_pinv(As, subn[s], 3, Ps)) { ok = false; break; }
       for (int r = 0; r < subn[s]; ++r) {
-        m.subidx[((int64_t)s * KM + r) * nc + c] = (uint8_t)sub[s][r];
-        for (int a = 0; a < 3; ++a) m.pinvm[((int64_t)(s * 3 + a) * KM + r) * nc + c] = Ps[a * subn[s] + r];
+        m.subidx[((int64_t)s * KM + r) * ncp + c] = (uint8_t)sub[s][r];
+        for (int a = 0; a < 3; ++a) m.pinvm[((int64_t)(s * 3 + a) * KM + r) * ncp + c] = Ps[a * subn[s] + r];
       }
     }
     if (!ok) {
@@ -651,7 +653,7 @@ int build_host_mesh(const hgks_mesh_desc& d, HostMesh& m, std::string& err) {
     }
     for (int k = 0; k < K; ++k) m.sten[(int64_t)k * nc + c] = k < n ? big[k].id : (int32_t)c;
     for (int dd = 0; dd < 9; ++dd)
-      for (int k = 0; k < n; ++k) m.pinv0[((int64_t)dd * K + k) * nc + c] = P0[dd * n + k];
+      for (int k = 0; k < n; ++k) m.pinv0[((int64_t)dd * K + k) * ncp + c] = P0[dd * n + k];
   }
   if (fail >= 0) {
     std::snprintf(buf, sizeof buf, "%s at cell %lld (caller index %lld)", fail_msg, (long long)fail,
@@ -664,16 +666,16 @@ int build_host_mesh(const hgks_mesh_desc& d, HostMesh& m, std::string& err) {
 
 int64_t device_bytes(const HostMesh& m, int precision) {
   auto al = [](int64_t b) { return (b + 255) / 256 * 256; };
-  const int64_t nc = m.nc, nf = m.nf, ng = m.ng, nce = nc + ng;
+  const int64_t nc = m.nc, nf = m.nf, ng = m.ng, nce = nc + ng, ncp = m.ncp;
   const int64_t rs = precision == HGKS_FP32_MIXED ? 4 : 8;
   int64_t b = 0;
   // static mesh data
   b += al(8 * nc) * 4;                         // vol, hdt, hinv, (spare)
   b += al(8 * 3 * nc) + al(8 * 6 * nc);        // cen, mom
   b += al(4 * (int64_t)m.K * nc);              // sten
-  b += al(8 * (int64_t)9 * m.K * nc);          // pinv0
-  b += al((int64_t)m.M * m.KM * nc);           // subidx
-  b += al(8 * (int64_t)m.M * 3 * m.KM * nc);   // pinvm
+  b += al(8 * (int64_t)9 * m.K * ncp);         // pinv0
+  b += al((int64_t)m.M * m.KM * ncp);          // subidx
+  b += al(8 * (int64_t)m.M * 3 * m.KM * ncp);  // pinvm
   b += al(4 * (int64_t)m.nfc * nc);            // cface
   b += al(4 * ng) * 2 + al(8 * 3 * ng);        // ghosts
   b += al(4 * nf) * 2;                         // fown, fnbr

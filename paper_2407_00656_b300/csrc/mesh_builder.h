@@ -22,6 +22,8 @@ struct HostMesh {
   int KM = 0;      // padded sub-stencil size: 6 (tet) or 3 (hex)
   int K = 0;       // padded big-stencil size (max over cells)
   int64_t nc = 0, nf = 0, ng = 0;
+  int64_t ncp = 0;  // row pitch of pinv0, subidx, pinvm: nc rounded up to 32, so that
+                    // 32 consecutive cells of a row start on a 256-byte boundary
 
   // cell order: new index -> caller index
   std::vector<int64_t> perm;
@@ -36,9 +38,9 @@ struct HostMesh {
   std::vector<double> mom;       // [6][nc] central second moments / h^2 (xx yy zz xy yz zx)
   std::vector<double> hinv;      // [nc] 1/h, h = |cell|^(1/3)
   std::vector<int32_t> sten;     // [K][nc] indices into cells+ghosts (padding: the cell itself)
-  std::vector<double> pinv0;     // [9*K][nc] quadratic least-squares inverse, row d col k at d*K+k
-  std::vector<uint8_t> subidx;   // [M*KM][nc] positions in the big stencil
-  std::vector<double> pinvm;     // [M*3*KM][nc] linear inverses, (m,d,r) at (m*3+d)*KM+r
+  std::vector<double> pinv0;     // [9*K][ncp] quadratic least-squares inverse, row d col k at d*K+k
+  std::vector<uint8_t> subidx;   // [M*KM][ncp] positions in the big stencil
+  std::vector<double> pinvm;     // [M*3*KM][ncp] linear inverses, (m,d,r) at (m*3+d)*KM+r
   std::vector<int32_t> cface;    // [nfc][nc] 2*face + (1 if the cell is the face's neighbour)
 
   // per ghost (one per physical boundary face)
