@@ -87,17 +87,24 @@ typedef struct {
  *   precision      HGKS_FP64, or HGKS_FP32_MIXED: reconstruction and flux
  *                  in binary32, geometry, inverses and S2O4 in binary64.
  *   use_graph      1: replay each step as one captured CUDA graph.
+ *   autotune       1: at hgks_init, time the kernel variants (register-capped
+ *                  or uncapped flux; reconstruction rows staged by bulk
+ *                  asynchronous copies or read directly) on this mesh and
+ *                  keep the fastest.  All variants give bitwise equal results.
  *   stream         cudaStream_t to run on, or NULL for a library stream. */
 typedef struct {
   double gamma, mu_ref, T_ref, visc_exp, Pr, cfl, tau_num_c, weno_eps, weno_gamma_lin;
   double q_inf[5];
   int32_t precision;
   int32_t use_graph;
+  int32_t autotune;
+  int32_t reserved;
   void* stream;
 } hgks_params;
 
 /* Fill *p with defaults: gamma 1.4, inviscid, Pr 1, cfl 0.4, weno_eps 1e-8,
- * weno_gamma_lin 0.025, q_inf = (1,0,0,0,2.5), FP64, graphs on, NULL stream. */
+ * weno_gamma_lin 0.025, q_inf = (1,0,0,0,2.5), FP64, graphs on, autotune off,
+ * NULL stream. */
 void hgks_params_default(hgks_params* p);
 
 /* Build the host mesh: faces, periodic pairing, boundary ghosts, two-layer
@@ -122,9 +129,40 @@ int64_t hgks_mesh_info(const hgks_mesh* mesh, int what);
  * it.  Device memory is one cudaMalloc arena sized by hgks_mesh_info(.,5|6). */
 int hgks_init(hgks_mesh* mesh, const hgks_params* params, const double* q0, hgks_solver** out);
 
+/* Batched solver (no counterpart in the paper; the batching of many small
+ * meshes into one launch per kernel): the n meshes form one disjoint union,
+ * so every kernel launch of a step covers all of them, while each member keeps
+ * its own time, CFL step, step counter and status.  All meshes must have the
+ * same cell type.  q0[i] is member i's [n_cells_i][5] state in its caller
+ * order.  On HGKS_OK the solver owns (and frees) all the meshes; on failure
+ * the caller still owns them.  hgks_step advances every member; members whose
+ * t_end is reached stop.  hgks_read / hgks_write address member 0. */
+int hgks_batch_init(hgks_mesh* const* meshes, int n, const hgks_params* params, const double* const* q0,
+                    hgks_solver** out);
+
+/* Number of member meshes of a solver (1 for hgks_init), or -1. */
+int hgks_members(const hgks_solver* s);
+
 /* Replace the state with q ([n_cells][5] host, caller order) at time t and
- * reset the step counter (restart / resume). */
+ * reset the step counter (restart / resume).  Synchronises. */
 int hgks_write(hgks_solver* s, const double* q, double t);
+
+/* hgks_write / hgks_read for one member of a batched solver. */
+int hgks_member_write(hgks_solver* s, int member, const double* q, double t);
+int hgks_member_read(hgks_solver* s, int member, double* q_out, double* t_out, int64_t* steps_out);
+
+/* Non-blocking: 1 if all queued work of the solver has finished, 0 if some
+ * is still running, a negative code on error. */
+int hgks_query(hgks_solver* s);
+
+/* Kernel variants in use (see hgks_params.autotune): flux_variant 0
+ * uncapped / 1 register-capped; recon_variant 0 staged / 1 direct. */
+int hgks_tuning(const hgks_solver* s, int* flux_variant, int* recon_variant);
+/* Select the variants by hand (0 or 1 each); synchronises. */
+int hgks_set_tuning(hgks_solver* s, int flux_variant, int recon_variant);
+
+/* Device bytes held by the solver (its single arena), or -1. */
+int64_t hgks_solver_bytes(const hgks_solver* s);
 
 /* Advance n_steps S2O4 steps asynchronously on the solver's stream (Algorithm
  * 2: time step, then two stages of reconstruction, flux and update).

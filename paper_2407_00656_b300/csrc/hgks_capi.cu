@@ -18,8 +18,16 @@ struct hgks_mesh {
   hgks::HostMesh m;
 };
 
+// One member mesh of a solver: its cells occupy [coff, coff + nc) of the
+// solver's (union) cell numbering; perm maps its cells to caller order.
+struct Member {
+  int64_t coff = 0, nc = 0;
+  std::vector<int64_t> perm;
+};
+
 struct hgks_solver {
-  hgks::HostMesh mesh;
+  hgks::HostMesh mesh;          // the mesh, or the disjoint union of a batch
+  std::vector<Member> members;
   hgks::DevMesh dm{};
   hgks::DevParams dp{};
   hgks::DevWork dw{};
@@ -84,18 +92,17 @@ int check_params(const hgks_params* p) {
   return HGKS_OK;
 }
 
-// caller order [n][5] -> internal SoA [5][stride] (new order)
-void to_internal(const hgks::HostMesh& m, const double* q, std::vector<double>& h, int64_t stride) {
-  h.assign(5 * stride, 0.0);
-  for (int64_t c = 0; c < m.nc; ++c) {
-    const double* s = q + 5 * m.perm[c];
-    for (int v = 0; v < 5; ++v) h[v * stride + c] = s[v];
+// member's caller order [n][5] -> internal SoA [5][stride] at the member's offset
+void to_internal(const Member& mb, const double* q, std::vector<double>& h, int64_t stride) {
+  for (int64_t c = 0; c < mb.nc; ++c) {
+    const double* s = q + 5 * mb.perm[c];
+    for (int v = 0; v < 5; ++v) h[v * stride + mb.coff + c] = s[v];
   }
 }
-void to_caller(const hgks::HostMesh& m, const double* h, int64_t stride, double* q) {
-  for (int64_t c = 0; c < m.nc; ++c) {
-    double* d = q + 5 * m.perm[c];
-    for (int v = 0; v < 5; ++v) d[v] = h[v * stride + c];
+void to_caller(const Member& mb, const double* h, int64_t stride, double* q) {
+  for (int64_t c = 0; c < mb.nc; ++c) {
+    double* d = q + 5 * mb.perm[c];
+    for (int v = 0; v < 5; ++v) d[v] = h[v * stride + mb.coff + c];
   }
 }
 
@@ -123,6 +130,7 @@ void hgks_params_default(hgks_params* p) {
   p->q_inf[4] = 2.5;
   p->precision = HGKS_FP64;
   p->use_graph = 1;
+  p->autotune = 0;
   p->stream = nullptr;
 }
 
@@ -172,8 +180,23 @@ int64_t hgks_mesh_info(const hgks_mesh* mesh, int what) {
   }
 }
 
-int hgks_init(hgks_mesh* mesh, const hgks_params* params, const double* q0, hgks_solver** out) {
-  if (!mesh || !out || !q0) return fail(HGKS_EINVAL, "NULL argument");
+}  // extern "C"
+
+namespace {
+
+// Device bytes of a solver over the (union) mesh m with nmesh members.
+int64_t solver_bytes(const hgks::HostMesh& m, int precision, int nmesh) {
+  int64_t b = hgks::device_bytes(m, precision);
+  if (nmesh > 1) b += (4 * m.nc + 255) / 256 * 256;
+  b += ((int64_t)sizeof(hgks::Control) * nmesh + 255) / 256 * 256;
+  return b;
+}
+
+// Build a solver over the given meshes (one, or a batch).  On HGKS_OK the
+// solver owns the meshes and the caller's handles are deleted; on failure the
+// caller's meshes are untouched.
+int create_solver(hgks_mesh* const* meshes, int n, const hgks_params* params, const double* const* q0,
+                  hgks_solver** out) {
   *out = nullptr;
   int rc = check_params(params);
   if (rc) return rc;
@@ -186,16 +209,46 @@ int hgks_init(hgks_mesh* mesh, const hgks_params* params, const double* q0, hgks
   auto bail = [&](int code) {
     if (s->arena) cudaFree(s->arena);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
-    // hand the mesh back to the caller untouched
-    std::swap(mesh->m, s->mesh);
+    if (n == 1) std::swap(meshes[0]->m, s->mesh);  // hand a single mesh back untouched
     delete s;
     return code;
   };
-  std::swap(s->mesh, mesh->m);
+  std::vector<int32_t> cmesh;
+  try {
+    if (n == 1) {
+      std::swap(s->mesh, meshes[0]->m);
+      Member mb;
+      mb.coff = 0;
+      mb.nc = s->mesh.nc;
+      mb.perm = s->mesh.perm;
+      s->members.push_back(std::move(mb));
+    } else {
+      std::vector<const hgks::HostMesh*> parts;
+      for (int i = 0; i < n; ++i) parts.push_back(&meshes[i]->m);
+      std::vector<int64_t> coff;
+      std::string err;
+      rc = hgks::build_union(parts, s->mesh, cmesh, coff, err);
+      if (rc) { g_err = err; return bail(rc); }
+      if (!hgks::stencil_supported(s->mesh.nfc, s->mesh.K)) {
+        g_err = "batch stencil size is not among the compiled shapes";
+        return bail(HGKS_EMESH);
+      }
+      for (int i = 0; i < n; ++i) {
+        Member mb;
+        mb.coff = coff[i];
+        mb.nc = meshes[i]->m.nc;
+        mb.perm = meshes[i]->m.perm;
+        s->members.push_back(std::move(mb));
+      }
+    }
+  } catch (const std::bad_alloc&) {
+    g_err = "host allocation failed while building the batch";
+    return bail(HGKS_ENOMEM);
+  }
   const hgks::HostMesh& m = s->mesh;
   s->precision = params->precision;
   s->use_graph = params->use_graph;
-  const size_t bytes = (size_t)hgks::device_bytes(m, s->precision);
+  const size_t bytes = (size_t)solver_bytes(m, s->precision, n);
   cudaError_t e = cudaMalloc(&s->arena, bytes);
   if (e != cudaSuccess) {
     s->arena = nullptr;
@@ -218,12 +271,13 @@ int hgks_init(hgks_mesh* mesh, const hgks_params* params, const double* q0, hgks
   hgks::DevMesh& dm = s->dm;
   dm.nc = m.nc; dm.nf = m.nf; dm.ng = m.ng; dm.nce = m.nc + m.ng; dm.ncp = m.ncp;
   dm.K = m.K; dm.M = m.M; dm.KM = m.KM; dm.G = m.G; dm.nfc = m.nfc;
+  dm.nmesh = n;
   std::vector<double> volinv(m.nc);
   for (int64_t c = 0; c < m.nc; ++c) volinv[c] = 1.0 / m.vol[c];
   double* p_volinv = cv.take<double>(m.nc);
   double* p_hdt = cv.take<double>(m.nc);
   double* p_hinv = cv.take<double>(m.nc);
-  cv.take<double>(m.nc);  // spare slot kept by the size formula
+  cv.take<double>(m.nc);      // spare slot kept by the size formula
   cv.take<double>(3 * m.nc);  // centroids are baked into the face offsets; slot kept for the size formula
   double* p_mom = cv.take<double>(6 * m.nc);
   int32_t* p_sten = cv.take<int32_t>((int64_t)m.K * m.nc);
@@ -248,11 +302,14 @@ int hgks_init(hgks_mesh* mesh, const hgks_params* params, const double* q0, hgks
   const int64_t rs = s->precision == HGKS_FP32_MIXED ? 4 : 8;
   w.coef = cv.take<char>(rs * 50 * m.nc);
   w.Fs = cv.take<char>(rs * 10 * m.nf);
-  w.ctl = cv.take<hgks::Control>(1);
+  int32_t* p_cmesh = n > 1 ? cv.take<int32_t>(m.nc) : nullptr;
+  hgks::Control* p_ctl = cv.take<hgks::Control>(n);
+  w.ctl = p_ctl;
   if (cv.off > bytes) { g_err = "internal error: arena too small"; return bail(HGKS_ENOMEM); }
   dm.volinv = p_volinv; dm.hdt = p_hdt; dm.hinv = p_hinv; dm.mom = p_mom; dm.sten = p_sten; dm.pinv0 = p_pinv0;
   dm.subidx = p_subidx; dm.pinvm = p_pinvm; dm.cface = p_cface; dm.gsrc = p_gsrc; dm.gtag = p_gtag; dm.gnrm = p_gnrm;
   dm.fown = p_fown; dm.fnbr = p_fnbr; dm.fdl = p_fdl; dm.fdr = p_fdr; dm.fn = p_fn; dm.fw = p_fw;
+  dm.cmesh = p_cmesh;
   cudaError_t ue = cudaSuccess;
   auto chk = [&](cudaError_t x) { if (ue == cudaSuccess) ue = x; };
   chk(up(p_volinv, volinv));
@@ -275,6 +332,7 @@ int hgks_init(hgks_mesh* mesh, const hgks_params* params, const double* q0, hgks
   chk(up(p_fdr, m.fdr));
   chk(up(p_fn, m.fn));
   chk(up(p_fw, m.fw));
+  if (p_cmesh) chk(up(p_cmesh, cmesh));
   chk(cudaMemset(w.Q, 0, sizeof(double) * 5 * dm.nce));
   chk(cudaMemset(w.Qs, 0, sizeof(double) * 5 * dm.nce));
   if (ue != cudaSuccess) { cuda_fail(ue, "uploading the mesh"); return bail(HGKS_ECUDA); }
@@ -292,38 +350,101 @@ int hgks_init(hgks_mesh* mesh, const hgks_params* params, const double* q0, hgks
   dp.glin = params->weno_gamma_lin;
   for (int i = 0; i < 5; ++i) dp.qinf[i] = params->q_inf[i];
   dp.viscous = (params->mu_ref > 0.0 || params->tau_num_c > 0.0) ? 1 : 0;
+  dp.flux_variant = 0;
+  dp.recon_variant = 0;
   hgks::prepare_kernels(dm, s->precision);
-  // initial state
-  to_internal(m, q0, s->hbuf, dm.nce);
+  // initial states
+  s->hbuf.assign(5 * dm.nce, 0.0);
+  for (int i = 0; i < n; ++i) to_internal(s->members[i], q0[i], s->hbuf, dm.nce);
   e = cudaMemcpyAsync(w.Q, s->hbuf.data(), sizeof(double) * 5 * dm.nce, cudaMemcpyHostToDevice, s->stream);
   if (e != cudaSuccess) { cuda_fail(e, "copying the initial state"); return bail(HGKS_ECUDA); }
-  hgks::launch_reset(dm, dp, w, s->precision, 0.0, s->stream);
+  hgks::launch_reset(dm, dp, w, s->precision, -1, 0.0, s->stream);
   e = cudaStreamSynchronize(s->stream);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) { cuda_fail(e, "initialising the solver"); return bail(HGKS_ECUDA); }
-  // the solver now owns the mesh: leave the caller's handle empty and free it
-  delete mesh;
+  if (params->autotune) {
+    // time every variant pair on this mesh and state (the state is not
+    // modified: only the reconstruction and flux work arrays are written)
+    hgks::launch_setdt(dm, w, 1e-3, s->stream);
+    float best = -1.f;
+    int bf = 0, br = 0;
+    for (int fv = 0; fv < 2; ++fv)
+      for (int rv = 0; rv < 2; ++rv) {
+        dp.flux_variant = fv;
+        dp.recon_variant = rv;
+        hgks::time_stage(dm, dp, w, s->precision, 1, s->stream);  // warm-up
+        const float ms = hgks::time_stage(dm, dp, w, s->precision, 3, s->stream);
+        if (ms >= 0.f && (best < 0.f || ms < best)) { best = ms; bf = fv; br = rv; }
+      }
+    dp.flux_variant = bf;
+    dp.recon_variant = br;
+    hgks::launch_setdt(dm, w, 0.0, s->stream);
+    e = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) { cuda_fail(e, "autotuning"); return bail(HGKS_ECUDA); }
+  }
+  for (int i = 0; i < n; ++i) delete meshes[i];  // the solver holds the mesh data (or a union of copies)
   *out = s;
   return HGKS_OK;
 }
 
-int hgks_write(hgks_solver* s, const double* q, double t) {
+int read_flags(hgks_solver* s, int only, hgks::Control* first) {
+  std::vector<hgks::Control> c(s->members.size());
+  HGKS_CUDA(cudaMemcpy(c.data(), s->dw.ctl, sizeof(hgks::Control) * c.size(), cudaMemcpyDeviceToHost),
+            "reading the control blocks");
+  if (first) *first = c[only >= 0 ? only : 0];
+  for (size_t i = 0; i < c.size(); ++i) {
+    if (only >= 0 && (int)i != only) continue;
+    if (c[i].flags & hgks::FLAG_TIMEOUT) return fail(HGKS_ETIMEOUT, "a bounded wait for staged copies ran out");
+    if (c[i].flags & hgks::FLAG_NONFINITE) return fail(HGKS_ENONFINITE, "a step produced a non-finite cell average");
+  }
+  // a staging timeout is recorded on member 0 for the whole solver
+  if (only > 0 && (c[0].flags & hgks::FLAG_TIMEOUT)) return fail(HGKS_ETIMEOUT, "a bounded wait for staged copies ran out");
+  return HGKS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hgks_init(hgks_mesh* mesh, const hgks_params* params, const double* q0, hgks_solver** out) {
+  if (!mesh || !out || !q0) return fail(HGKS_EINVAL, "NULL argument");
+  return create_solver(&mesh, 1, params, &q0, out);
+}
+
+int hgks_batch_init(hgks_mesh* const* meshes, int n, const hgks_params* params, const double* const* q0,
+                    hgks_solver** out) {
+  if (!meshes || !q0 || !out || n <= 0) return fail(HGKS_EINVAL, "bad argument");
+  for (int i = 0; i < n; ++i)
+    if (!meshes[i] || !q0[i]) return fail(HGKS_EINVAL, "NULL member mesh or state");
+  return create_solver(meshes, n, params, q0, out);
+}
+
+int hgks_members(const hgks_solver* s) { return s ? (int)s->members.size() : -1; }
+
+int hgks_member_write(hgks_solver* s, int member, const double* q, double t) {
   if (!s || !q) return fail(HGKS_EINVAL, "NULL argument");
-  to_internal(s->mesh, q, s->hbuf, s->dm.nce);
+  if (member < 0 || member >= (int)s->members.size()) return fail(HGKS_EINVAL, "member out of range");
   HGKS_CUDA(cudaStreamSynchronize(s->stream), "waiting for queued work");
+  s->hbuf.resize(5 * s->dm.nce);
+  HGKS_CUDA(cudaMemcpy(s->hbuf.data(), s->dw.Q, sizeof(double) * 5 * s->dm.nce, cudaMemcpyDeviceToHost),
+            "reading the state");
+  to_internal(s->members[member], q, s->hbuf, s->dm.nce);
   HGKS_CUDA(cudaMemcpyAsync(s->dw.Q, s->hbuf.data(), sizeof(double) * 5 * s->dm.nce, cudaMemcpyHostToDevice, s->stream),
             "copying the state");
-  hgks::launch_reset(s->dm, s->dp, s->dw, s->precision, t, s->stream);
+  hgks::launch_reset(s->dm, s->dp, s->dw, s->precision, member, t, s->stream);
   HGKS_CUDA(cudaStreamSynchronize(s->stream), "writing the state");
   HGKS_CUDA(cudaGetLastError(), "writing the state");
   return HGKS_OK;
 }
 
+int hgks_write(hgks_solver* s, const double* q, double t) { return hgks_member_write(s, 0, q, t); }
+
 int hgks_step(hgks_solver* s, int n_steps, double t_end, double dt_fixed) {
   if (!s) return fail(HGKS_EINVAL, "NULL solver");
   if (n_steps < 0) return fail(HGKS_EINVAL, "n_steps must be >= 0");
   if (n_steps == 0) return HGKS_OK;
-  hgks::launch_control(s->dw, t_end, dt_fixed, s->stream);
+  hgks::launch_control(s->dm, s->dw, t_end, dt_fixed, s->stream);
   if (s->use_graph) {
     if (!s->graph) {
       cudaGraph_t g = nullptr;
@@ -346,38 +467,49 @@ int hgks_step(hgks_solver* s, int n_steps, double t_end, double dt_fixed) {
   return HGKS_OK;
 }
 
+int hgks_query(hgks_solver* s) {
+  if (!s) return fail(HGKS_EINVAL, "NULL solver");
+  cudaError_t e = cudaStreamQuery(s->stream);
+  if (e == cudaSuccess) return 1;
+  if (e == cudaErrorNotReady) {
+    cudaGetLastError();
+    return 0;
+  }
+  return cuda_fail(e, "querying the stream");
+}
+
 int hgks_sync(hgks_solver* s) {
   if (!s) return fail(HGKS_EINVAL, "NULL solver");
   HGKS_CUDA(cudaStreamSynchronize(s->stream), "synchronising");
   HGKS_CUDA(cudaGetLastError(), "synchronising");
-  hgks::Control c;
-  HGKS_CUDA(cudaMemcpy(&c, s->dw.ctl, sizeof c, cudaMemcpyDeviceToHost), "reading the control block");
-  if (c.flags & hgks::FLAG_TIMEOUT) return fail(HGKS_ETIMEOUT, "a bounded wait for staged copies ran out");
-  if (c.flags & hgks::FLAG_NONFINITE) return fail(HGKS_ENONFINITE, "a step produced a non-finite cell average");
-  return HGKS_OK;
+  return read_flags(s, -1, nullptr);
 }
 
-int hgks_read(hgks_solver* s, double* q_out, double* t_out, int64_t* steps_out) {
+int hgks_member_read(hgks_solver* s, int member, double* q_out, double* t_out, int64_t* steps_out) {
   if (!s) return fail(HGKS_EINVAL, "NULL solver");
+  if (member < 0 || member >= (int)s->members.size()) return fail(HGKS_EINVAL, "member out of range");
   HGKS_CUDA(cudaStreamSynchronize(s->stream), "synchronising");
-  hgks::Control c;
-  HGKS_CUDA(cudaMemcpy(&c, s->dw.ctl, sizeof c, cudaMemcpyDeviceToHost), "reading the control block");
   if (q_out) {
     s->hbuf.resize(5 * s->dm.nce);
     HGKS_CUDA(cudaMemcpy(s->hbuf.data(), s->dw.Q, sizeof(double) * 5 * s->dm.nce, cudaMemcpyDeviceToHost),
               "reading the state");
-    to_caller(s->mesh, s->hbuf.data(), s->dm.nce, q_out);
+    to_caller(s->members[member], s->hbuf.data(), s->dm.nce, q_out);
   }
+  hgks::Control c;
+  const int rc = read_flags(s, member, &c);
   if (t_out) *t_out = c.t;
   if (steps_out) *steps_out = c.steps;
-  if (c.flags & hgks::FLAG_TIMEOUT) return fail(HGKS_ETIMEOUT, "a bounded wait for staged copies ran out");
-  if (c.flags & hgks::FLAG_NONFINITE) return fail(HGKS_ENONFINITE, "a step produced a non-finite cell average");
-  return HGKS_OK;
+  return rc;
+}
+
+int hgks_read(hgks_solver* s, double* q_out, double* t_out, int64_t* steps_out) {
+  return hgks_member_read(s, 0, q_out, t_out, steps_out);
 }
 
 int hgks_stage_operator(hgks_solver* s, double dt, double* L_out, double* dL_out) {
   if (!s || !L_out || !dL_out) return fail(HGKS_EINVAL, "NULL argument");
   if (!(dt > 0.0)) return fail(HGKS_EINVAL, "dt must be positive");
+  if (s->members.size() != 1) return fail(HGKS_EINVAL, "the stage operator is defined for single-mesh solvers");
   const int64_t nc = s->dm.nc;
   // the stage buffers Q* and R are free between steps
   hgks::launch_operator(s->dm, s->dp, s->dw, s->precision, dt, s->dw.Qs, s->dw.R, s->stream);
@@ -385,9 +517,9 @@ int hgks_stage_operator(hgks_solver* s, double dt, double* L_out, double* dL_out
   HGKS_CUDA(cudaGetLastError(), "evaluating the stage operator");
   std::vector<double> h(5 * nc);
   HGKS_CUDA(cudaMemcpy(h.data(), s->dw.Qs, sizeof(double) * 5 * nc, cudaMemcpyDeviceToHost), "reading L");
-  to_caller(s->mesh, h.data(), nc, L_out);
+  to_caller(s->members[0], h.data(), nc, L_out);
   HGKS_CUDA(cudaMemcpy(h.data(), s->dw.R, sizeof(double) * 5 * nc, cudaMemcpyDeviceToHost), "reading dL/dt");
-  to_caller(s->mesh, h.data(), nc, dL_out);
+  to_caller(s->members[0], h.data(), nc, dL_out);
   return HGKS_OK;
 }
 
@@ -396,7 +528,7 @@ int hgks_profile(hgks_solver* s, int n_steps, double t_end, double dt_fixed, dou
   hgks::StepEvents ev;
   for (int i = 0; i < 8; ++i) HGKS_CUDA(cudaEventCreate(&ev.ev[i]), "creating events");
   double acc[4] = {0, 0, 0, 0};
-  hgks::launch_control(s->dw, t_end, dt_fixed, s->stream);
+  hgks::launch_control(s->dm, s->dw, t_end, dt_fixed, s->stream);
   int rc = HGKS_OK;
   for (int k = 0; k < n_steps && rc == HGKS_OK; ++k) {
     hgks::launch_step(s->dm, s->dp, s->dw, s->precision, s->stream, &ev);
@@ -412,6 +544,29 @@ int hgks_profile(hgks_solver* s, int n_steps, double t_end, double dt_fixed, dou
   for (int i = 0; i < 8; ++i) cudaEventDestroy(ev.ev[i]);
   for (int i = 0; i < 4; ++i) ms_out[i] = acc[i] / n_steps;
   return rc;
+}
+
+int64_t hgks_solver_bytes(const hgks_solver* s) { return s ? (int64_t)s->arena_bytes : -1; }
+
+int hgks_set_tuning(hgks_solver* s, int flux_variant, int recon_variant) {
+  if (!s) return fail(HGKS_EINVAL, "NULL solver");
+  if (flux_variant < 0 || flux_variant > 1 || recon_variant < 0 || recon_variant > 1)
+    return fail(HGKS_EINVAL, "variant out of range");
+  HGKS_CUDA(cudaStreamSynchronize(s->stream), "waiting for queued work");
+  s->dp.flux_variant = flux_variant;
+  s->dp.recon_variant = recon_variant;
+  if (s->graph) {  // the captured step used the previous variants
+    cudaGraphExecDestroy(s->graph);
+    s->graph = nullptr;
+  }
+  return HGKS_OK;
+}
+
+int hgks_tuning(const hgks_solver* s, int* flux_variant, int* recon_variant) {
+  if (!s) return fail(HGKS_EINVAL, "NULL solver");
+  if (flux_variant) *flux_variant = s->dp.flux_variant;
+  if (recon_variant) *recon_variant = s->dp.recon_variant;
+  return HGKS_OK;
 }
 
 void hgks_destroy(hgks_solver* s) {

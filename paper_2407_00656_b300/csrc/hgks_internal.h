@@ -13,6 +13,8 @@ namespace hgks {
 struct DevMesh {
   int64_t nc, nf, ng, nce;  // cells, faces, ghosts, cells + ghosts
   int64_t ncp;              // row pitch of pinv0, subidx, pinvm (nc rounded up to 32)
+  int nmesh;                // member meshes of a batch (1 for a single mesh)
+  const int32_t* cmesh;     // [nc] member of each cell, or nullptr when nmesh == 1
   int K, M, KM, G, nfc;
   const double* volinv;   // [nc] 1/|cell|
   const double* hdt;      // [nc]
@@ -39,6 +41,9 @@ struct DevParams {
   double gamma, Kint, mu_ref, T_ref, visc_exp, Pr, cfl, tau_c, eps, glin;
   double qinf[5];
   int viscous;  // 1 when mu_ref > 0 or tau_c > 0 (collision time may be non-zero)
+  // kernel variants chosen by the autotuner (results are bitwise identical):
+  int flux_variant;   // 0: registers uncapped, 1: capped for 4 blocks of 128 per SM
+  int recon_variant;  // 0: rows staged by bulk async copies, 1: rows read directly
 };
 
 // Step control block in device memory.
@@ -63,12 +68,17 @@ struct DevWork {
   float* Qf;      // [5][nce] binary32 copy of the stage state (mixed precision only)
   void* coef;     // [50][nc] reconstruction polynomials (double or float)
   void* Fs;       // [10][nf] face flux sums: F (5) then dF/dt (5) (double or float)
-  Control* ctl;
+  Control* ctl;   // [nmesh] one control block per member mesh
 };
 
 // Message returned by hgks_last_error() on this thread.
 void set_last_error(const std::string& msg);
 
+// Set the step size of every member (tuning and test paths).
+void launch_setdt(const DevMesh& m, const DevWork& w, double dt, cudaStream_t s);
+// Time `reps` stage evaluations (reconstruction + flux) of the current state
+// with the variants in p; returns milliseconds per evaluation (< 0 on error).
+float time_stage(const DevMesh& m, const DevParams& p, const DevWork& w, int precision, int reps, cudaStream_t s);
 // Per-instantiation kernel attributes; call once per solver before capture.
 void prepare_kernels(const DevMesh& m, int precision);
 // True if the kernels are compiled for this stencil shape (faces per cell, K).
@@ -83,11 +93,12 @@ struct StepEvents {
 // Launch one S2O4 step (Algorithm 2) on stream s; precision 0 = FP64, 1 = mixed.
 void launch_step(const DevMesh& m, const DevParams& p, const DevWork& w, int precision, cudaStream_t s,
                  const StepEvents* ev = nullptr);
-// Set t_end and dt_fixed for the following steps.
-void launch_control(const DevWork& w, double t_end, double dt_fixed, cudaStream_t s);
-// Reset time/steps/flags, copy the binary32 state if needed and compute the
-// first step bound of the current state.
-void launch_reset(const DevMesh& m, const DevParams& p, const DevWork& w, int precision, double t, cudaStream_t s);
+// Set t_end and dt_fixed of every member for the following steps.
+void launch_control(const DevMesh& m, const DevWork& w, double t_end, double dt_fixed, cudaStream_t s);
+// Reset time/steps/flags of member `only` (every member when only < 0), copy
+// the binary32 state if needed and compute the step bounds of the state.
+void launch_reset(const DevMesh& m, const DevParams& p, const DevWork& w, int precision, int only, double t,
+                  cudaStream_t s);
 // L and dL/dt of the current state for step dt into Qs[0:5] and R (as L) -- test path.
 void launch_operator(const DevMesh& m, const DevParams& p, const DevWork& w, int precision, double dt,
                      double* L, double* dL, cudaStream_t s);

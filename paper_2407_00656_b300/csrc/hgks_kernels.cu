@@ -434,12 +434,19 @@ __device__ __forceinline__ void farfield(const R q[5], const R qinf[5], const R 
 // --------------------------------------------------------------------------
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 
-__global__ void k_control(Control* c, double t_end, double dt_fixed) {
-  c->t_end = t_end;
-  c->dt_fixed = dt_fixed;
+// Control kernels run one thread per member mesh.
+__global__ void k_control(Control* ctl, int n, double t_end, double dt_fixed) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  ctl[i].t_end = t_end;
+  ctl[i].dt_fixed = dt_fixed;
 }
 
-__global__ void k_reset(Control* c, double t) {
+// Reset member `only` (or every member when only < 0) to time t.
+__global__ void k_reset(Control* ctl, int n, int only, double t) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || (only >= 0 && i != only)) return;
+  Control* c = ctl + i;
   c->t = t;
   c->dt = 0.0;
   c->steps = 0;
@@ -447,7 +454,10 @@ __global__ void k_reset(Control* c, double t) {
   c->dtmin_bits = dbits(__longlong_as_double(0x7ff0000000000000LL));
 }
 
-__global__ void k_finalize(Control* c, double cfl) {
+__global__ void k_finalize(Control* ctl, int n, double cfl) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  Control* c = ctl + i;
   double dt = c->dt_fixed > 0.0 ? c->dt_fixed : cfl * __longlong_as_double((long long)c->dtmin_bits);
   if (c->t_end > 0.0) dt = fmin(dt, c->t_end - c->t);
   if (!(dt > 0.0) || !(dt < 1e300)) dt = 0.0;
@@ -487,24 +497,51 @@ __device__ __forceinline__ void block_min_to(unsigned long long* dst, double v) 
   }
 }
 
-__global__ void __launch_bounds__(kBlock) k_dt(DevMesh m, DevParams P, const double* __restrict__ Q, Control* c) {
+// Minimum of v over the cells of each member mesh into ctl[member].dtmin_bits.
+// Called by every thread of the block (mid = -1 for threads without a cell).
+// One mesh: a block reduction; a batch: a warp reduction segmented by member
+// (the minimum of positive doubles is the minimum of their bit patterns,
+// reduced as the high word, then the low word among the lanes that hold it).
+__device__ __forceinline__ void member_min_to(const DevMesh& m, Control* ctl, int mid, double v) {
+  if (m.nmesh == 1) {
+    block_min_to(&ctl[0].dtmin_bits, v);
+    return;
+  }
+  const unsigned long long b = dbits(v);
+  const unsigned grp = __match_any_sync(0xffffffffu, mid);
+  const unsigned hi = (unsigned)(b >> 32);
+  const unsigned hmin = __reduce_min_sync(grp, hi);
+  const unsigned cand = grp & __ballot_sync(0xffffffffu, hi == hmin);
+  if (hi == hmin) {
+    const unsigned lmin = __reduce_min_sync(cand, (unsigned)b);
+    if ((int)(threadIdx.x & 31) == __ffs(cand) - 1 && mid >= 0 && hmin < 0x7ff00000u)
+      atomicMin(&ctl[mid].dtmin_bits, ((unsigned long long)hmin << 32) | lmin);
+  }
+}
+
+__device__ __forceinline__ int member_of(const DevMesh& m, int64_t c) { return m.cmesh ? m.cmesh[c] : 0; }
+
+__global__ void __launch_bounds__(kBlock) k_dt(DevMesh m, DevParams P, const double* __restrict__ Q, Control* ctl) {
   const int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x;
   double v = __longlong_as_double(0x7ff0000000000000LL);
+  int mid = -1;
   if (i < m.nc) {
+    mid = member_of(m, i);
     double q[5];
     for (int k = 0; k < 5; ++k) q[k] = Q[k * m.nce + i];
     v = cell_dt(q, m.hdt[i], P);
     if (!(v >= 0.0)) v = __longlong_as_double(0x7ff0000000000000LL);
   }
-  block_min_to(&c->dtmin_bits, v);
+  member_min_to(m, ctl, mid, v);
 }
 
 // Ghost cell averages: the boundary map of the mirrored interior cell.
 __global__ void __launch_bounds__(kBlock) k_ghost(DevMesh m, DevParams P, double* __restrict__ Q, float* __restrict__ Qf,
-                                                  const Control* __restrict__ c) {
+                                                  const Control* __restrict__ ctl) {
   const int64_t g = (int64_t)blockIdx.x * kBlock + threadIdx.x;
-  if (g >= m.ng || c->dt == 0.0) return;
+  if (g >= m.ng) return;
   const int64_t s = m.gsrc[g];
+  if (ctl[member_of(m, s)].dt == 0.0) return;
   double q[5], o[5];
   for (int k = 0; k < 5; ++k) q[k] = Q[k * m.nce + s];
   if (m.gtag[g] == 3) {  // wall: momentum reversed
@@ -638,32 +675,35 @@ struct ReconSmem {
   static constexpr size_t bytes = tile + sub + dq;
 };
 
-template <typename Real, typename QT, int K, int M, int KM>
+template <typename Real, typename QT, int K, int M, int KM, bool STAGE>
 __global__ void __launch_bounds__(kRThreads) k_recon(DevMesh m, DevParams P, const QT* __restrict__ Q,
                                                      Real* __restrict__ coef, Control* __restrict__ ctl) {
   using S = ReconSmem<Real, K, M, KM>;
   constexpr int kRows = S::kRows;
   extern __shared__ __align__(128) unsigned char smem_raw[];
+  // staged variant: [tile | ssub | sdq]; direct variant: [sdq] only
   double* tile = reinterpret_cast<double*>(smem_raw);                // [kRows][kRC]
   uint8_t* ssub = smem_raw + S::tile;                                // [M*KM][kRC]
-  Real* sdq = reinterpret_cast<Real*>(smem_raw + S::tile + S::sub);  // [5][K][kRC]
+  Real* sdq = reinterpret_cast<Real*>(STAGE ? smem_raw + S::tile + S::sub : smem_raw);  // [5][K][kRC]
   __shared__ __align__(8) uint64_t bar;
-  if (ctl->dt == 0.0) return;  // uniform over the grid
+  if (m.nmesh == 1 && ctl->dt == 0.0) return;  // uniform over the grid (a batch computes every member)
   const int64_t nc = m.nc, ncp = m.ncp;
   const int lane = threadIdx.x & 31, v = threadIdx.x >> 5;
   const int64_t c0 = (int64_t)blockIdx.x * kRC;
   const int64_t c = c0 + lane;
   const bool valid = c < nc;
-  if (threadIdx.x == 0) mbar_init(&bar, 1);
-  __syncthreads();
-  if (v == 0) {
-    if (lane == 0) mbar_expect_tx(&bar, (uint32_t)(S::tile + S::sub));
-    __syncwarp();
-    for (int r = lane; r < kRows; r += 32) {
-      const double* src = r < 9 * K ? m.pinv0 + (int64_t)r * ncp + c0 : m.pinvm + (int64_t)(r - 9 * K) * ncp + c0;
-      bulk_g2s(tile + r * kRC, src, kRC * sizeof(double), &bar);
+  if constexpr (STAGE) {
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (v == 0) {
+      if (lane == 0) mbar_expect_tx(&bar, (uint32_t)(S::tile + S::sub));
+      __syncwarp();
+      for (int r = lane; r < kRows; r += 32) {
+        const double* src = r < 9 * K ? m.pinv0 + (int64_t)r * ncp + c0 : m.pinvm + (int64_t)(r - 9 * K) * ncp + c0;
+        bulk_g2s(tile + r * kRC, src, kRC * sizeof(double), &bar);
+      }
+      for (int r = lane; r < M * KM; r += 32) bulk_g2s(ssub + r * kRC, m.subidx + (int64_t)r * ncp + c0, kRC, &bar);
     }
-    for (int r = lane; r < M * KM; r += 32) bulk_g2s(ssub + r * kRC, m.subidx + (int64_t)r * ncp + c0, kRC, &bar);
   }
   // this warp's variable: stencil differences (overlaps the staging)
   Real qv = Real(0);
@@ -675,27 +715,39 @@ __global__ void __launch_bounds__(kRThreads) k_recon(DevMesh m, DevParams P, con
       sdq[(v * K + k) * kRC + lane] = (Real)Q[v * m.nce + j] - qv;
     }
   }
-  const bool ok = __syncthreads_and(mbar_wait_bounded(&bar, 0));
-  if (!ok) {
-    if (threadIdx.x == 0) atomicOr(&ctl->flags, FLAG_TIMEOUT);
-    mbar_wait_bounded(&bar, 0);  // copies in flight: a second bounded wait before leaving
-    return;
-  }
-  if constexpr (sizeof(Real) == 4) {
-    // binary32: convert the staged rows in place (low word of each slot), once
-    float* tf = reinterpret_cast<float*>(tile);
-    for (int e = threadIdx.x; e < kRows * kRC; e += kRThreads) tf[2 * e] = cvt<float>(tile[e]);
-    __syncthreads();
+  if constexpr (STAGE) {
+    const bool ok = __syncthreads_and(mbar_wait_bounded(&bar, 0));
+    if (!ok) {
+      if (threadIdx.x == 0) atomicOr(&ctl->flags, FLAG_TIMEOUT);
+      mbar_wait_bounded(&bar, 0);  // copies in flight: a second bounded wait before leaving
+      return;
+    }
+    if constexpr (sizeof(Real) == 4) {
+      // binary32: convert the staged rows in place (low word of each slot), once
+      float* tf = reinterpret_cast<float*>(tile);
+      for (int e = threadIdx.x; e < kRows * kRC; e += kRThreads) tf[2 * e] = cvt<float>(tile[e]);
+      __syncthreads();
+    }
+  } else {
+    __syncwarp();
   }
   if (!valid) return;
   auto row = [&](int r) -> Real {
-    if constexpr (sizeof(Real) == 4) return reinterpret_cast<const float*>(tile)[2 * (r * kRC + lane)];
-    else return tile[r * kRC + lane];
+    if constexpr (!STAGE)
+      return cvt<Real>(r < 9 * K ? m.pinv0[(int64_t)r * ncp + c] : m.pinvm[(int64_t)(r - 9 * K) * ncp + c]);
+    else if constexpr (sizeof(Real) == 4)
+      return reinterpret_cast<const float*>(tile)[2 * (r * kRC + lane)];
+    else
+      return tile[r * kRC + lane];
+  };
+  auto subpos = [&](int r) -> int {
+    if constexpr (STAGE) return ssub[r * kRC + lane];
+    else return m.subidx[(int64_t)r * ncp + c];
   };
   Real dq[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) dq[k] = sdq[(v * K + k) * kRC + lane];
-  // least-squares polynomials
+  // least-squares polynomials (the same operation order in both variants)
   Real a[9];
 #pragma unroll
   for (int d = 0; d < 9; ++d) {
@@ -709,7 +761,7 @@ __global__ void __launch_bounds__(kRThreads) k_recon(DevMesh m, DevParams P, con
   for (int s = 0; s < M; ++s) {
     Real x[KM];
 #pragma unroll
-    for (int r = 0; r < KM; ++r) x[r] = sdq[(v * K + ssub[(s * KM + r) * kRC + lane]) * kRC + lane];
+    for (int r = 0; r < KM; ++r) x[r] = sdq[(v * K + subpos(s * KM + r)) * kRC + lane];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       Real acc = Real(0);
@@ -748,13 +800,14 @@ __device__ __forceinline__ void eval_poly(const Real* __restrict__ coef, int64_t
 // Face flux, one thread per face: sum over the Gauss points of weight*area
 // times the flux of Eq. (flux), F and dF/dt in the global frame, oriented
 // from the owner to the neighbour.  Output Fs[j*nf + f], j = 0..4 F, 5..9 dF.
-template <typename Real, int G, bool VISC>
-__global__ void __launch_bounds__(kBlock) k_flux(DevMesh m, DevParams P, const Real* __restrict__ coef,
-                                                 Real* __restrict__ Fs, const Control* __restrict__ ctl) {
+template <typename Real, int G, bool VISC, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_flux(DevMesh m, DevParams P, const Real* __restrict__ coef,
+                                                       Real* __restrict__ Fs, const Control* __restrict__ ctl) {
   const int64_t nf = m.nf, nc = m.nc;
   const int64_t f = (int64_t)blockIdx.x * kBlock + threadIdx.x;
-  const double dtd = ctl->dt;
-  if (f >= nf || dtd == 0.0) return;
+  if (f >= nf) return;
+  const double dtd = ctl[member_of(m, m.fown[f])].dt;
+  if (dtd == 0.0) return;
   const Real dt = (Real)dtd;
   FluxParams<Real> FP;
   FP.gamma = (Real)P.gamma;
@@ -889,8 +942,9 @@ __global__ void __launch_bounds__(kBlock) k_update1(DevMesh m, const Real* __res
                                                    double* __restrict__ Qs, double* __restrict__ R,
                                                    float* __restrict__ Qf, const Control* __restrict__ ctl) {
   const int64_t c = (int64_t)blockIdx.x * kBlock + threadIdx.x;
-  const double dt = ctl->dt;
-  if (c >= m.nc || dt == 0.0) return;
+  if (c >= m.nc) return;
+  const double dt = ctl[member_of(m, c)].dt;
+  if (dt == 0.0) return;
   double L[5], dL[5];
   gather<Real, NFC>(m, Fs, c, L, dL);
 #pragma unroll
@@ -909,10 +963,11 @@ __global__ void __launch_bounds__(kBlock) k_update2(DevMesh m, DevParams P, cons
                                                    double* __restrict__ Q, const double* __restrict__ R,
                                                    float* __restrict__ Qf, Control* __restrict__ ctl) {
   const int64_t c = (int64_t)blockIdx.x * kBlock + threadIdx.x;
-  const double dt = ctl->dt;
-  if (dt == 0.0) return;  // uniform across the grid: no thread reaches the block reduction
+  if (m.nmesh == 1 && ctl->dt == 0.0) return;  // uniform: no thread reaches the block reduction
   double bound = __longlong_as_double(0x7ff0000000000000LL);
-  if (c < m.nc) {
+  const int mid = c < m.nc ? member_of(m, c) : -1;
+  const double dt = mid >= 0 ? ctl[mid].dt : 0.0;
+  if (dt != 0.0) {
     double L[5], dL[5];
     gather<Real, NFC>(m, Fs, c, L, dL);
     double q[5];
@@ -924,11 +979,11 @@ __global__ void __launch_bounds__(kBlock) k_update2(DevMesh m, DevParams P, cons
       Q[v * m.nce + c] = q[v];
       if (Qf) Qf[v * m.nce + c] = (float)q[v];
     }
-    if (!finite) atomicOr(&ctl->flags, FLAG_NONFINITE);
+    if (!finite) atomicOr(&ctl[mid].flags, FLAG_NONFINITE);
     bound = cell_dt(q, m.hdt[c], P);
     if (!(bound >= 0.0)) bound = __longlong_as_double(0x7ff0000000000000LL);
   }
-  block_min_to(&ctl->dtmin_bits, bound);
+  member_min_to(m, ctl, dt != 0.0 ? mid : -1, bound);
 }
 
 // Binary32 copy of the state (mixed precision).
@@ -937,7 +992,10 @@ __global__ void k_tofloat(const double* __restrict__ Q, float* __restrict__ Qf, 
   if (i < n) Qf[i] = (float)Q[i];
 }
 
-__global__ void k_setdt(Control* c, double dt) { c->dt = dt; }
+__global__ void k_setdt(Control* ctl, int n, double dt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) ctl[i].dt = dt;
+}
 
 // L and dL/dt of the state (test path).
 template <typename Real, int NFC>
@@ -954,13 +1012,15 @@ inline unsigned blocks(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock)
 template <typename Real, typename QT, int K, int M, int KM>
 void recon_launch(const DevMesh& m, const DevParams& p, const QT* Q, Real* coef, Control* ctl, cudaStream_t s,
                   bool prep) {
-  const size_t smem = ReconSmem<Real, K, M, KM>::bytes;
+  using S = ReconSmem<Real, K, M, KM>;
   if (prep) {
-    cudaFuncSetAttribute(k_recon<Real, QT, K, M, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_recon<Real, QT, K, M, KM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
+    cudaFuncSetAttribute(k_recon<Real, QT, K, M, KM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::dq);
     return;
   }
   const unsigned nb = (unsigned)((m.nc + kRC - 1) / kRC);
-  k_recon<Real, QT, K, M, KM><<<nb, kRThreads, smem, s>>>(m, p, Q, coef, ctl);
+  if (p.recon_variant == 1) k_recon<Real, QT, K, M, KM, false><<<nb, kRThreads, S::dq, s>>>(m, p, Q, coef, ctl);
+  else k_recon<Real, QT, K, M, KM, true><<<nb, kRThreads, S::bytes, s>>>(m, p, Q, coef, ctl);
 }
 
 // Stencil shapes compiled in: tetrahedra with 12..16 members and 4 sub-stencils
@@ -1004,18 +1064,23 @@ void recon_any(const DevMesh& m, const DevParams& p, const QT* Q, Real* coef, Co
   else recon_hex<Real, QT>(m, p, Q, coef, ctl, s, prep);
 }
 
-template <typename Real>
-void flux_any(const DevMesh& m, const DevParams& p, const Real* coef, Real* Fs, const Control* ctl, cudaStream_t s) {
+template <typename Real, int G, bool VISC>
+void flux_launch(const DevMesh& m, const DevParams& p, const Real* coef, Real* Fs, const Control* ctl, cudaStream_t s) {
   const unsigned nb = blocks(m.nf);
-  if (m.G == 3) {
-    if (p.viscous) k_flux<Real, 3, true><<<nb, kBlock, 0, s>>>(m, p, coef, Fs, ctl);
-    else k_flux<Real, 3, false><<<nb, kBlock, 0, s>>>(m, p, coef, Fs, ctl);
-  } else {
-    if (p.viscous) k_flux<Real, 4, true><<<nb, kBlock, 0, s>>>(m, p, coef, Fs, ctl);
-    else k_flux<Real, 4, false><<<nb, kBlock, 0, s>>>(m, p, coef, Fs, ctl);
-  }
+  if (p.flux_variant == 1) k_flux<Real, G, VISC, 4><<<nb, kBlock, 0, s>>>(m, p, coef, Fs, ctl);
+  else k_flux<Real, G, VISC, 1><<<nb, kBlock, 0, s>>>(m, p, coef, Fs, ctl);
 }
 
+template <typename Real>
+void flux_any(const DevMesh& m, const DevParams& p, const Real* coef, Real* Fs, const Control* ctl, cudaStream_t s) {
+  if (m.G == 3) {
+    if (p.viscous) flux_launch<Real, 3, true>(m, p, coef, Fs, ctl, s);
+    else flux_launch<Real, 3, false>(m, p, coef, Fs, ctl, s);
+  } else {
+    if (p.viscous) flux_launch<Real, 4, true>(m, p, coef, Fs, ctl, s);
+    else flux_launch<Real, 4, false>(m, p, coef, Fs, ctl, s);
+  }
+}
 template <typename Real>
 void stage_pair(const DevMesh& m, const DevParams& p, const DevWork& w, bool mixed, cudaStream_t s,
                 const StepEvents* ev) {
@@ -1048,17 +1113,44 @@ void stage_pair(const DevMesh& m, const DevParams& p, const DevWork& w, bool mix
 
 }  // namespace
 
+void launch_setdt(const DevMesh& m, const DevWork& w, double dt, cudaStream_t s) {
+  k_setdt<<<(m.nmesh + 127) / 128, 128, 0, s>>>(w.ctl, m.nmesh, dt);
+}
+
+float time_stage(const DevMesh& m, const DevParams& p, const DevWork& w, int precision, int reps, cudaStream_t s) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return -1.f;
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return -1.f; }
+  cudaEventRecord(e0, s);
+  for (int r = 0; r < reps; ++r) {
+    if (precision == 1) {
+      recon_any<float, float>(m, p, w.Qf, static_cast<float*>(w.coef), w.ctl, s);
+      flux_any<float>(m, p, static_cast<float*>(w.coef), static_cast<float*>(w.Fs), w.ctl, s);
+    } else {
+      recon_any<double, double>(m, p, w.Q, static_cast<double*>(w.coef), w.ctl, s);
+      flux_any<double>(m, p, static_cast<double*>(w.coef), static_cast<double*>(w.Fs), w.ctl, s);
+    }
+  }
+  cudaEventRecord(e1, s);
+  float ms = -1.f;
+  if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return reps > 0 && ms >= 0.f ? ms / reps : -1.f;
+}
+
 void prepare_kernels(const DevMesh& m, int precision) {
   if (precision == 1) recon_any<float, float>(m, DevParams{}, nullptr, nullptr, nullptr, 0, true);
   else recon_any<double, double>(m, DevParams{}, nullptr, nullptr, nullptr, 0, true);
 }
 
-void launch_control(const DevWork& w, double t_end, double dt_fixed, cudaStream_t s) {
-  k_control<<<1, 1, 0, s>>>(w.ctl, t_end, dt_fixed);
+void launch_control(const DevMesh& m, const DevWork& w, double t_end, double dt_fixed, cudaStream_t s) {
+  k_control<<<(m.nmesh + 127) / 128, 128, 0, s>>>(w.ctl, m.nmesh, t_end, dt_fixed);
 }
 
-void launch_reset(const DevMesh& m, const DevParams& p, const DevWork& w, int precision, double t, cudaStream_t s) {
-  k_reset<<<1, 1, 0, s>>>(w.ctl, t);
+void launch_reset(const DevMesh& m, const DevParams& p, const DevWork& w, int precision, int only, double t,
+                  cudaStream_t s) {
+  k_reset<<<(m.nmesh + 127) / 128, 128, 0, s>>>(w.ctl, m.nmesh, only, t);
   if (precision == 1) k_tofloat<<<blocks(5 * m.nce), kBlock, 0, s>>>(w.Q, w.Qf, 5 * m.nce);
   k_dt<<<blocks(m.nc), kBlock, 0, s>>>(m, p, w.Q, w.ctl);
 }
@@ -1066,7 +1158,7 @@ void launch_reset(const DevMesh& m, const DevParams& p, const DevWork& w, int pr
 void launch_step(const DevMesh& m, const DevParams& p, const DevWork& w, int precision, cudaStream_t s,
                  const StepEvents* ev) {
   if (ev) cudaEventRecord(ev->ev[0], s);
-  k_finalize<<<1, 1, 0, s>>>(w.ctl, p.cfl);
+  k_finalize<<<(m.nmesh + 127) / 128, 128, 0, s>>>(w.ctl, m.nmesh, p.cfl);
   if (ev) cudaEventRecord(ev->ev[1], s);
   if (precision == 1) stage_pair<float>(m, p, w, true, s, ev);
   else stage_pair<double>(m, p, w, false, s, ev);
@@ -1074,7 +1166,7 @@ void launch_step(const DevMesh& m, const DevParams& p, const DevWork& w, int pre
 
 void launch_operator(const DevMesh& m, const DevParams& p, const DevWork& w, int precision, double dt, double* L,
                      double* dL, cudaStream_t s) {
-  k_setdt<<<1, 1, 0, s>>>(w.ctl, dt);
+  k_setdt<<<(m.nmesh + 127) / 128, 128, 0, s>>>(w.ctl, m.nmesh, dt);
   const bool mixed = precision == 1;
   float* Qf = mixed ? w.Qf : nullptr;
   if (m.ng) k_ghost<<<blocks(m.ng), kBlock, 0, s>>>(m, p, w.Q, Qf, w.ctl);

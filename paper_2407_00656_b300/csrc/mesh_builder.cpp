@@ -664,6 +664,77 @@ int build_host_mesh(const hgks_mesh_desc& d, HostMesh& m, std::string& err) {
   return HGKS_OK;
 }
 
+int build_union(const std::vector<const HostMesh*>& parts, HostMesh& u, std::vector<int32_t>& cmesh,
+                std::vector<int64_t>& coff, std::string& err) {
+  if (parts.empty()) { err = "empty batch"; return HGKS_EINVAL; }
+  const HostMesh& a = *parts[0];
+  u = HostMesh();
+  u.ctype = a.ctype; u.nfc = a.nfc; u.G = a.G; u.M = a.M; u.KM = a.KM;
+  int64_t nc = 0, nf = 0, ng = 0;
+  int K = 0;
+  std::vector<int64_t> foff, goff;
+  coff.clear();
+  for (const HostMesh* p : parts) {
+    if (p->ctype != a.ctype) { err = "a batch needs one cell type"; return HGKS_EINVAL; }
+    coff.push_back(nc); foff.push_back(nf); goff.push_back(ng);
+    nc += p->nc; nf += p->nf; ng += p->ng;
+    K = std::max(K, p->K);
+  }
+  if (nc >= (int64_t(1) << 30) || nf >= (int64_t(1) << 30)) { err = "batch too large"; return HGKS_EINVAL; }
+  u.nc = nc; u.nf = nf; u.ng = ng; u.K = K;
+  const int64_t ncp = (nc + 31) / 32 * 32;
+  u.ncp = ncp;
+  const int M = u.M, KM = u.KM, G = u.G, nfc = u.nfc;
+  cmesh.assign(nc, 0);
+  u.vol.resize(nc); u.hdt.resize(nc); u.hinv.resize(nc); u.cen.resize(3 * nc); u.mom.resize(6 * nc);
+  u.sten.assign((int64_t)K * nc, 0);
+  u.pinv0.assign((int64_t)9 * K * ncp, 0.0);
+  u.subidx.assign((int64_t)M * KM * ncp, 0);
+  u.pinvm.assign((int64_t)M * 3 * KM * ncp, 0.0);
+  u.cface.resize((int64_t)nfc * nc);
+  u.gsrc.resize(ng); u.gtag.resize(ng); u.gnrm.resize(3 * ng);
+  u.fown.resize(nf); u.fnbr.resize(nf);
+  u.fdl.resize((int64_t)G * 3 * nf); u.fdr.resize((int64_t)G * 3 * nf); u.fn.resize((int64_t)G * 3 * nf);
+  u.fw.resize((int64_t)G * nf);
+  for (size_t i = 0; i < parts.size(); ++i) {
+    const HostMesh& p = *parts[i];
+    const int64_t co = coff[i], fo = foff[i], go = goff[i];
+    for (int64_t c = 0; c < p.nc; ++c) {
+      const int64_t uc = co + c;
+      cmesh[uc] = (int32_t)i;
+      u.vol[uc] = p.vol[c]; u.hdt[uc] = p.hdt[c]; u.hinv[uc] = p.hinv[c];
+      for (int a3 = 0; a3 < 3; ++a3) u.cen[a3 * nc + uc] = p.cen[a3 * p.nc + c];
+      for (int q = 0; q < 6; ++q) u.mom[q * nc + uc] = p.mom[q * p.nc + c];
+      for (int k = 0; k < K; ++k) {
+        int64_t j = k < p.K ? p.sten[k * p.nc + c] : c;  // padding: the cell itself
+        u.sten[k * nc + uc] = (int32_t)(j < p.nc ? co + j : nc + go + (j - p.nc));
+      }
+      for (int d = 0; d < 9; ++d)
+        for (int k = 0; k < p.K; ++k) u.pinv0[((int64_t)d * K + k) * ncp + uc] = p.pinv0[((int64_t)d * p.K + k) * p.ncp + c];
+      for (int r = 0; r < M * KM; ++r) u.subidx[(int64_t)r * ncp + uc] = p.subidx[(int64_t)r * p.ncp + c];
+      for (int r = 0; r < M * 3 * KM; ++r) u.pinvm[(int64_t)r * ncp + uc] = p.pinvm[(int64_t)r * p.ncp + c];
+      for (int q = 0; q < nfc; ++q) u.cface[q * nc + uc] = (int32_t)(p.cface[q * p.nc + c] + 2 * fo);
+    }
+    for (int64_t g = 0; g < p.ng; ++g) {
+      u.gsrc[go + g] = (int32_t)(co + p.gsrc[g]);
+      u.gtag[go + g] = p.gtag[g];
+      for (int a3 = 0; a3 < 3; ++a3) u.gnrm[a3 * ng + go + g] = p.gnrm[a3 * p.ng + g];
+    }
+    for (int64_t f = 0; f < p.nf; ++f) {
+      const int64_t uf = fo + f;
+      u.fown[uf] = (int32_t)(co + p.fown[f]);
+      u.fnbr[uf] = p.fnbr[f] >= 0 ? (int32_t)(co + p.fnbr[f]) : p.fnbr[f];
+      for (int r = 0; r < G * 3; ++r) {
+        u.fdl[r * nf + uf] = p.fdl[r * p.nf + f];
+        u.fdr[r * nf + uf] = p.fdr[r * p.nf + f];
+        u.fn[r * nf + uf] = p.fn[r * p.nf + f];
+      }
+      for (int r = 0; r < G; ++r) u.fw[r * nf + uf] = p.fw[r * p.nf + f];
+    }
+  }
+  return HGKS_OK;
+}
+
 int64_t device_bytes(const HostMesh& m, int precision) {
   auto al = [](int64_t b) { return (b + 255) / 256 * 256; };
   const int64_t nc = m.nc, nf = m.nf, ng = m.ng, nce = nc + ng, ncp = m.ncp;

@@ -61,6 +61,13 @@ struct HostMesh {
 // a message in err.
 int build_host_mesh(const hgks_mesh_desc& d, HostMesh& m, std::string& err);
 
+// Disjoint union of member meshes of one cell type: cells, ghosts and faces
+// concatenated member by member (cell offsets in coff), stencils padded to
+// the largest K, cmesh[c] = member of union cell c.  perm of the union is left
+// empty; each member keeps its own.
+int build_union(const std::vector<const HostMesh*>& parts, HostMesh& u, std::vector<int32_t>& cmesh,
+                std::vector<int64_t>& coff, std::string& err);
+
 // Device bytes a solver for this mesh allocates (precision HGKS_FP64 or
 // HGKS_FP32_MIXED), including alignment padding.
 int64_t device_bytes(const HostMesh& m, int precision);

@@ -46,7 +46,7 @@ class hgks_params(C.Structure):
         ("gamma", C.c_double), ("mu_ref", C.c_double), ("T_ref", C.c_double), ("visc_exp", C.c_double),
         ("Pr", C.c_double), ("cfl", C.c_double), ("tau_num_c", C.c_double), ("weno_eps", C.c_double),
         ("weno_gamma_lin", C.c_double), ("q_inf", C.c_double * 5), ("precision", C.c_int32),
-        ("use_graph", C.c_int32), ("stream", C.c_void_p),
+        ("use_graph", C.c_int32), ("autotune", C.c_int32), ("reserved", C.c_int32), ("stream", C.c_void_p),
     ]
 
 
@@ -59,8 +59,9 @@ class HGKSError(RuntimeError):
 _lib = None
 _lock = threading.Lock()
 EXPORTS = ("hgks_params_default", "hgks_mesh_create", "hgks_mesh_destroy", "hgks_mesh_info", "hgks_init",
-           "hgks_write", "hgks_step", "hgks_sync", "hgks_read", "hgks_stage_operator", "hgks_profile",
-           "hgks_destroy", "hgks_last_error")
+           "hgks_batch_init", "hgks_members", "hgks_write", "hgks_member_write", "hgks_step", "hgks_query",
+           "hgks_sync", "hgks_read", "hgks_member_read", "hgks_stage_operator", "hgks_profile", "hgks_solver_bytes",
+           "hgks_tuning", "hgks_set_tuning", "hgks_destroy", "hgks_last_error", "hgks_cfl_dt_noalloc")
 
 
 def lib():
@@ -81,6 +82,17 @@ def lib():
             L.hgks_mesh_info.restype = C.c_int64
             L.hgks_init.argtypes = [vp, C.POINTER(hgks_params), dp, C.POINTER(vp)]
             L.hgks_write.argtypes = [vp, dp, C.c_double]
+            L.hgks_batch_init.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(hgks_params), C.POINTER(dp), C.POINTER(vp)]
+            L.hgks_members.argtypes = [vp]
+            L.hgks_member_write.argtypes = [vp, C.c_int, dp, C.c_double]
+            L.hgks_member_read.argtypes = [vp, C.c_int, dp, dp, C.POINTER(C.c_int64)]
+            L.hgks_query.argtypes = [vp]
+            L.hgks_solver_bytes.argtypes = [vp]
+            L.hgks_solver_bytes.restype = C.c_int64
+            L.hgks_tuning.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+            L.hgks_tuning.restype = C.c_int
+            L.hgks_set_tuning.argtypes = [vp, C.c_int, C.c_int]
+            L.hgks_set_tuning.restype = C.c_int
             L.hgks_step.argtypes = [vp, C.c_int, C.c_double, C.c_double]
             L.hgks_sync.argtypes = [vp]
             L.hgks_read.argtypes = [vp, dp, dp, C.POINTER(C.c_int64)]
@@ -92,7 +104,8 @@ def lib():
             L.hgks_destroy.restype = None
             L.hgks_last_error.restype = C.c_char_p
             for name in ("hgks_mesh_create", "hgks_init", "hgks_write", "hgks_step", "hgks_sync", "hgks_read",
-                         "hgks_stage_operator", "hgks_profile"):
+                         "hgks_stage_operator", "hgks_profile", "hgks_batch_init", "hgks_members",
+                         "hgks_member_write", "hgks_member_read", "hgks_query"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -203,17 +216,64 @@ class Mesh:
 
 
 class Solver:
-    """hgks_init / hgks_step / hgks_read / hgks_destroy on one mesh."""
+    """hgks_init / hgks_step / hgks_read / hgks_destroy on one mesh, or
+    hgks_batch_init on a list of meshes (one launch per kernel for all)."""
 
-    def __init__(self, mesh: Mesh, q0, params: hgks_params | None = None, **kw):
-        self.n_cells = mesh.n_cells
+    def __init__(self, mesh, q0, params: hgks_params | None = None, **kw):
         p = params if params is not None else make_params(**kw)
-        q0 = np.ascontiguousarray(q0, dtype=np.float64).reshape(self.n_cells, 5)
         h = C.c_void_p()
-        _check(lib().hgks_init(mesh._h, C.byref(p), _dp(q0), C.byref(h)), "hgks_init")
-        mesh.release()
+        if isinstance(mesh, (list, tuple)):
+            meshes = list(mesh)
+            self.member_cells = [m.n_cells for m in meshes]
+            qs = [np.ascontiguousarray(q, dtype=np.float64).reshape(n, 5) for q, n in zip(q0, self.member_cells)]
+            harr = (C.c_void_p * len(meshes))(*[m._h for m in meshes])
+            qarr = (C.POINTER(C.c_double) * len(qs))(*[_dp(q) for q in qs])
+            _check(lib().hgks_batch_init(harr, len(meshes), C.byref(p), qarr, C.byref(h)), "hgks_batch_init")
+            for m in meshes:
+                m.release()
+        else:
+            self.member_cells = [mesh.n_cells]
+            q0 = np.ascontiguousarray(q0, dtype=np.float64).reshape(mesh.n_cells, 5)
+            _check(lib().hgks_init(mesh._h, C.byref(p), _dp(q0), C.byref(h)), "hgks_init")
+            mesh.release()
+        self.n_cells = self.member_cells[0]
         self._h = h
         self.params = p
+
+    @property
+    def members(self) -> int:
+        return len(self.member_cells)
+
+    def member_read(self, i: int, out=None):
+        q = out if out is not None else np.empty((self.member_cells[i], 5))
+        t = C.c_double()
+        s = C.c_int64()
+        _check(lib().hgks_member_read(self._h, int(i), _dp(q), C.byref(t), C.byref(s)), "hgks_member_read")
+        return q, t.value, s.value
+
+    def member_write(self, i: int, q, t: float = 0.0):
+        q = np.ascontiguousarray(q, dtype=np.float64).reshape(self.member_cells[i], 5)
+        _check(lib().hgks_member_write(self._h, int(i), _dp(q), float(t)), "hgks_member_write")
+
+    def query(self) -> bool:
+        rc = lib().hgks_query(self._h)
+        if rc < 0:
+            _check(rc, "hgks_query")
+        return rc == 1
+
+    @property
+    def device_bytes(self) -> int:
+        return int(lib().hgks_solver_bytes(self._h))
+
+    @property
+    def tuning(self):
+        """(flux_variant, recon_variant) in use."""
+        f, r = C.c_int(), C.c_int()
+        _check(lib().hgks_tuning(self._h, C.byref(f), C.byref(r)), "hgks_tuning")
+        return f.value, r.value
+
+    def set_tuning(self, flux_variant: int, recon_variant: int):
+        _check(lib().hgks_set_tuning(self._h, int(flux_variant), int(recon_variant)), "hgks_set_tuning")
 
     def step(self, n: int = 1, t_end: float = 0.0, dt_fixed: float = 0.0):
         _check(lib().hgks_step(self._h, int(n), float(t_end), float(dt_fixed)), "hgks_step")
