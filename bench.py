@@ -149,6 +149,86 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def mixed_vs_fp64(H, w, stream, K, W):
+    """FP32-mixed throughput on the same workload, and its L1 difference from
+    the FP64 path after 20 steps of the same fixed dt from the same state."""
+    import torch
+
+    nc = len(w["cells"])
+    s = H.Solver(H.Mesh(w["xyz"], w["cells"], w["periods"], w.get("bfn"), w.get("bft")), w["q"],
+                 precision=H.HGKS_FP32_MIXED, stream=stream.cuda_stream, **w["params"])
+    s.step(W)
+    s.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s.step(K)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = s.profile(K)
+    # precision: both paths from the initial state with the FP64 path's first dt
+    dts = []
+    out = {}
+    for prec in (H.HGKS_FP64, H.HGKS_FP32_MIXED):
+        t = H.Solver(H.Mesh(w["xyz"], w["cells"], w["periods"], w.get("bfn"), w.get("bft")), w["q"],
+                     precision=prec, **w["params"])
+        if not dts:
+            t.step(1)
+            dts.append(t.read()[1])
+            t.write(w["q"], 0.0)
+        t.step(20, dt_fixed=dts[0])
+        out[prec] = t.read()[0]
+        t.close()
+    vol = H.Mesh(w["xyz"], w["cells"], w["periods"], w.get("bfn"), w.get("bft")).geometry()[0]
+    a, b = out[H.HGKS_FP32_MIXED], out[H.HGKS_FP64]
+    l1 = {name: float((np.abs(a[:, v] - b[:, v]) * vol).sum() / (np.abs(b[:, v]) * vol).sum())
+          for name, v in (("rho", 0), ("rhoU", 1), ("rhoE", 4))}
+    linf = {name: float(np.abs(a[:, v] - b[:, v]).max() / np.abs(b[:, v]).max())
+            for name, v in (("rho", 0), ("rhoU", 1), ("rhoE", 4))}
+    s.close()
+    return {"value": nc * K / (ms * 1e-3), "unit": "cell-updates/s", "ms_per_step": ms / K, "dtype": "f32-mixed",
+            "kernel_ms_per_step": {"ghost+recon": prof[1], "flux": prof[2], "update": prof[3]},
+            "error_vs_fp64_after_20_steps": {"l1_rel": l1, "linf_rel": linf, "dt": dts[0]}}
+
+
+def serve_run(H, small: bool, capacity=None):
+    """Serving stream, FP32-mixed.  small: 48 requests of 5e3..1e5 cells (the
+    default line); otherwise the full 256 requests of 5e3..2e6 cells.  The
+    Poisson rate offers 0.8 x the measured mixed throughput."""
+    from paper_2407_00656_b300 import serve as S
+
+    import torch
+
+    n, hi = (48, 1e5) if small else (256, 2e6)
+    lo, steps = 5e3, 200
+    classes = 4 if small else 8
+    cache = S.MeshCache()
+    t0 = time.perf_counter()
+    cache.warm(S.c5_requests(n=n, lo=lo, hi=hi, steps=steps, rate=1.0, seed=0, classes=classes))
+    warm_s = time.perf_counter() - t0
+    free, total = torch.cuda.mem_get_info()
+    budget = int(0.8 * free)
+    # capacity of this request mix: every request present at t = 0 (closed loop)
+    burst = S.c5_requests(n=n, lo=lo, hi=hi, steps=steps, rate=1e9, seed=0, classes=classes)
+    S.Server(mem_budget=budget, precision=H.HGKS_FP32_MIXED, chunk_steps=10, cache=cache).run(burst, time_limit=1800)
+    cap = S.summarize(burst)["cell_updates_per_s"]
+    # open loop: Poisson arrivals offering 0.8 x that capacity
+    mean_work = np.mean([r.cells for r in burst]) * steps
+    rate = 0.8 * cap / mean_work
+    reqs = S.c5_requests(n=n, lo=lo, hi=hi, steps=steps, rate=rate, seed=0, classes=classes)
+    server = S.Server(mem_budget=budget, precision=H.HGKS_FP32_MIXED, chunk_steps=10, cache=cache)
+    server.run(reqs, time_limit=1800)
+    st = S.summarize(reqs)
+    st.update({"capacity_cell_updates_per_s": cap, "offered_rate_per_s": rate, "steps_per_request": steps,
+               "cells_range": [lo, hi],
+               "peak_resident_solves": server.peak_active, "peak_device_bytes": server.peak_used,
+               "mesh_cache_build_s": warm_s, "precision": "f32-mixed",
+               "mix": "half jittered density-wave cubes, half sphere shells at Re U[100,300]"})
+    return st
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -158,12 +238,28 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--workload", default="density48")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the small serving run of the default line")
+    ap.add_argument("--serve", action="store_true", help="run the full serving stream (256 requests, up to 2M cells)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.serve:
+        import torch
+
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        from paper_2407_00656_b300 import hgks as H
+
+        with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+            st = serve_run(H, small=False)
+        if rank == 0:
+            print(json.dumps({"metric": "serve p50/p99 latency (s) and aggregate cell-updates/s", "value": st["p99_s"],
+                              "unit": "s (p99)", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+                              "dtype": "f32-mixed", "config": {"workload": "serving stream, 256 requests"},
+                              "serve": st, "clocks": clk.summary()}), flush=True)
+        return
 
     import torch
 
@@ -243,6 +339,12 @@ def main():
     e2e = {"value": nc * e2e_steps * world / t_e2e, "unit": "cell-updates/s",
            "h2d_bytes_per_step": int(qh.nbytes), "d2h_bytes_per_step": int(out.nbytes)}
 
+    extra = {}
+    if args.precision == "fp64":
+        extra["mixed"] = mixed_vs_fp64(H, w, stream, K, W)
+    if not args.no_serve:
+        extra["serve"] = serve_run(H, small=True, capacity=extra.get("mixed", {}).get("value"))
+
     if rank == 0:
         line = {"metric": "cell-updates/s", "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": K,
                 "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
@@ -252,6 +354,7 @@ def main():
                            "parallelism": f"replicas x{world}"},
                 "roofline": roof, "e2e": e2e, "gpu_launches": K * launches_per_step + 1,
                 "clocks": clk.summary()}
+        line.update(extra)
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(w)
         print(json.dumps(line), flush=True)

@@ -118,6 +118,15 @@ int hgks_mesh_create(const hgks_mesh_desc* desc, hgks_mesh** out);
 /* Free a mesh that was never handed to hgks_init.  NULL is ignored. */
 void hgks_mesh_destroy(hgks_mesh* mesh);
 
+/* Cell volumes and time-step length scales 3|cell|/|surface| ([n_cells] host
+ * each, caller order; either pointer may be NULL), e.g. for volume-weighted
+ * error norms or hgks_cfl_dt_noalloc. */
+int hgks_mesh_geometry(const hgks_mesh* mesh, double* vol_out, double* hdt_out);
+
+/* Copy a built mesh (host memory only), e.g. to start several solvers on the
+ * same geometry without rebuilding it.  Errors: HGKS_EINVAL, HGKS_ENOMEM. */
+int hgks_mesh_clone(const hgks_mesh* mesh, hgks_mesh** out);
+
 /* Mesh facts: what = 0 cells, 1 faces, 2 boundary ghosts, 3 padded big
  * stencil size, 4 sub-stencil count, 5 device bytes hgks_init would allocate
  * for precision 0, 6 the same for precision 1.  Returns -1 for bad input. */

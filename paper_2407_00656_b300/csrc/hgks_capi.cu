@@ -165,6 +165,27 @@ int hgks_mesh_create(const hgks_mesh_desc* d, hgks_mesh** out) {
 
 void hgks_mesh_destroy(hgks_mesh* mesh) { delete mesh; }
 
+int hgks_mesh_geometry(const hgks_mesh* mesh, double* vol_out, double* hdt_out) {
+  if (!mesh) return fail(HGKS_EINVAL, "NULL mesh");
+  const hgks::HostMesh& m = mesh->m;
+  for (int64_t c = 0; c < m.nc; ++c) {
+    if (vol_out) vol_out[m.perm[c]] = m.vol[c];
+    if (hdt_out) hdt_out[m.perm[c]] = m.hdt[c];
+  }
+  return HGKS_OK;
+}
+
+int hgks_mesh_clone(const hgks_mesh* mesh, hgks_mesh** out) {
+  if (!mesh || !out) return fail(HGKS_EINVAL, "NULL argument");
+  *out = nullptr;
+  try {
+    *out = new hgks_mesh(*mesh);
+  } catch (const std::bad_alloc&) {
+    return fail(HGKS_ENOMEM, "host allocation failed while copying the mesh");
+  }
+  return HGKS_OK;
+}
+
 int64_t hgks_mesh_info(const hgks_mesh* mesh, int what) {
   if (!mesh) return -1;
   const hgks::HostMesh& m = mesh->m;
@@ -383,7 +404,14 @@ int create_solver(hgks_mesh* const* meshes, int n, const hgks_params* params, co
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) { cuda_fail(e, "autotuning"); return bail(HGKS_ECUDA); }
   }
-  for (int i = 0; i < n; ++i) delete meshes[i];  // the solver holds the mesh data (or a union of copies)
+  for (int i = 0; i < n; ++i) delete meshes[i];
+  // the device holds the mesh now; keep only the sizes on the host
+  {
+    hgks::HostMesh sizes;
+    sizes.ctype = m.ctype; sizes.nfc = m.nfc; sizes.G = m.G; sizes.M = m.M; sizes.KM = m.KM; sizes.K = m.K;
+    sizes.nc = m.nc; sizes.nf = m.nf; sizes.ng = m.ng; sizes.ncp = m.ncp;
+    s->mesh = std::move(sizes);
+  }
   *out = s;
   return HGKS_OK;
 }

@@ -58,7 +58,8 @@ class HGKSError(RuntimeError):
 
 _lib = None
 _lock = threading.Lock()
-EXPORTS = ("hgks_params_default", "hgks_mesh_create", "hgks_mesh_destroy", "hgks_mesh_info", "hgks_init",
+EXPORTS = ("hgks_params_default", "hgks_mesh_create", "hgks_mesh_destroy", "hgks_mesh_clone", "hgks_mesh_geometry", "hgks_mesh_info",
+           "hgks_init",
            "hgks_batch_init", "hgks_members", "hgks_write", "hgks_member_write", "hgks_step", "hgks_query",
            "hgks_sync", "hgks_read", "hgks_member_read", "hgks_stage_operator", "hgks_profile", "hgks_solver_bytes",
            "hgks_tuning", "hgks_set_tuning", "hgks_destroy", "hgks_last_error", "hgks_cfl_dt_noalloc")
@@ -78,6 +79,10 @@ def lib():
             L.hgks_mesh_create.argtypes = [C.POINTER(hgks_mesh_desc), C.POINTER(vp)]
             L.hgks_mesh_destroy.argtypes = [vp]
             L.hgks_mesh_destroy.restype = None
+            L.hgks_mesh_geometry.argtypes = [vp, dp, dp]
+            L.hgks_mesh_geometry.restype = C.c_int
+            L.hgks_mesh_clone.argtypes = [vp, C.POINTER(vp)]
+            L.hgks_mesh_clone.restype = C.c_int
             L.hgks_mesh_info.argtypes = [vp, C.c_int]
             L.hgks_mesh_info.restype = C.c_int64
             L.hgks_init.argtypes = [vp, C.POINTER(hgks_params), dp, C.POINTER(vp)]
@@ -202,6 +207,22 @@ class Mesh:
 
     def device_bytes(self, precision: int = HGKS_FP64) -> int:
         return self.info(5 if precision == HGKS_FP64 else 6)
+
+    def geometry(self):
+        """(cell volumes, 3|cell|/|surface|) in caller order."""
+        vol = np.empty(self.n_cells)
+        hdt = np.empty(self.n_cells)
+        _check(lib().hgks_mesh_geometry(self._h, _dp(vol), _dp(hdt)), "hgks_mesh_geometry")
+        return vol, hdt
+
+    def clone(self) -> "Mesh":
+        """hgks_mesh_clone: an independent copy of the built mesh."""
+        h = C.c_void_p()
+        _check(lib().hgks_mesh_clone(self._h, C.byref(h)), "hgks_mesh_clone")
+        m = Mesh.__new__(Mesh)
+        m._keep = []
+        m._h = h
+        return m
 
     def release(self):
         """Hand ownership to a solver (hgks_init took it)."""

@@ -1,0 +1,220 @@
+"""Continuous-batching request loop for HGKS solves on one GPU.
+
+Requests (a mesh, an initial state, physical parameters and a step count)
+arrive over time.  The loop
+  * admits waiting requests in arrival order while their device bytes fit the
+    memory budget (hgks_mesh_info / hgks_solver_bytes),
+  * packs small requests that share their parameters and arrive together
+    into one batched solver (hgks_batch_init: one launch per kernel for all
+    of them),
+  * keeps every admitted solve resident on the device, each solver on its own
+    CUDA stream, and interleaves their steps in chunks: a chunk is queued
+    whenever a solver's previous chunk has finished (hgks_query), so work of
+    different solves overlaps on the device and newly admitted solves start
+    while others are running,
+  * reads a finished solve back, frees its memory and records its latency
+    (completion time minus arrival time).
+
+All numerics run in libhgks; this module only schedules.  Built meshes are
+cached by geometry and cloned per request (hgks_mesh_clone), the warm-cache
+case of a service that sees the same geometries repeatedly.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import hgks as H
+from . import inputs as I
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float            # seconds after the start of the run
+    kind: str                 # "density" or "sphere"
+    size: int                 # lattice size N (density) or surface grid n (sphere)
+    steps: int
+    params: dict = field(default_factory=dict)
+    # filled by the server
+    admitted: float = math.nan
+    finished: float = math.nan
+    cells: int = 0
+    result: np.ndarray | None = None
+    t: float = math.nan
+    steps_done: int = 0
+
+
+def sphere_layers(n: int) -> int:
+    return max(2, int(round(1.3 * n)))
+
+
+def density_params():
+    return {}
+
+
+def sphere_params(re: float, mach: float = 0.2535):
+    return dict(q_inf=tuple(I.free_stream(mach)), mu_ref=mach / re, Pr=0.72, visc_exp=0.7, T_ref=1 / 1.4,
+                tau_num_c=1.0)
+
+
+class MeshCache:
+    """Built meshes and initial states by geometry key, cloned per request."""
+
+    def __init__(self):
+        self._m = {}
+
+    def get(self, kind: str, size: int):
+        mesh, q = self.peek(kind, size)
+        return mesh.clone(), q
+
+    def peek(self, kind: str, size: int):
+        """The cached mesh itself (not a copy) and its initial state."""
+        key = (kind, size)
+        if key not in self._m:
+            if kind == "density":
+                xyz, cells, per = I.kuhn_cube(size, jitter=0.15, seed=size)
+                mesh = H.Mesh(xyz, cells, per)
+                q = I.density_wave_state(xyz, cells, 0.0)
+            else:
+                xyz, cells, bfn, bft = I.sphere_shell(size, sphere_layers(size), seed=size)
+                mesh = H.Mesh(xyz, cells, None, bfn, bft)
+                q = np.tile(I.free_stream(0.2535), (len(cells), 1))
+            self._m[key] = (mesh, q)
+        return self._m[key]
+
+    def warm(self, requests):
+        for r in requests:
+            self.peek(r.kind, r.size)
+
+
+@dataclass
+class _Slot:
+    solver: H.Solver
+    reqs: list
+    remaining: int
+    bytes: int
+
+
+class Server:
+    def __init__(self, mem_budget: int, precision: int = H.HGKS_FP32_MIXED, chunk_steps: int = 10,
+                 small_cells: int = 100_000, max_batch: int = 16, cache: MeshCache | None = None):
+        self.mem_budget = int(mem_budget)
+        self.precision = precision
+        self.chunk = chunk_steps
+        self.small = small_cells
+        self.max_batch = max_batch
+        self.cache = cache or MeshCache()
+
+    def _params_key(self, r: Request):
+        return tuple(sorted((k, tuple(v) if isinstance(v, (list, tuple)) else v) for k, v in r.params.items()))
+
+    def run(self, requests, time_limit: float = 3600.0):
+        """Serve the requests (list of Request, arrival times relative to the
+        start); returns them with admitted/finished/result filled in."""
+        pending = sorted(requests, key=lambda r: r.arrival)
+        queue, active = [], []
+        used = 0
+        self.peak_used = 0
+        self.peak_active = 0
+        t0 = time.perf_counter()
+        pi = 0
+        while pi < len(pending) or queue or active:
+            now = time.perf_counter() - t0
+            if now > time_limit:
+                raise TimeoutError("serving run exceeded its time limit")
+            while pi < len(pending) and pending[pi].arrival <= now:
+                queue.append(pending[pi])
+                pi += 1
+            busy = False
+            # admission in arrival order while memory allows
+            while queue:
+                head = queue[0]
+                mesh, q = self.cache.peek(head.kind, head.size)
+                group = [(head, mesh, q)]
+                if mesh.n_cells < self.small:
+                    key = (head.kind, self._params_key(head), head.steps)
+                    for r in queue[1:]:
+                        if len(group) >= self.max_batch:
+                            break
+                        if (r.kind, self._params_key(r), r.steps) == key:
+                            m2, q2 = self.cache.peek(r.kind, r.size)
+                            if m2.n_cells < self.small:
+                                group.append((r, m2, q2))
+                need = sum(m.device_bytes(self.precision) for _, m, _ in group) + 65536 * len(group)
+                if used + need > self.mem_budget:
+                    if not active:
+                        raise MemoryError(f"request {head.rid} needs {need} bytes, budget {self.mem_budget}")
+                    break
+                meshes = [m.clone() for _, m, _ in group]
+                states = [qq for _, _, qq in group]
+                solver = H.Solver(meshes if len(group) > 1 else meshes[0], states if len(group) > 1 else states[0],
+                                  precision=self.precision, **head.params)
+                nb = solver.device_bytes
+                used += nb
+                tnow = time.perf_counter() - t0
+                for r, m, _ in group:
+                    r.admitted = tnow
+                    queue.remove(r)
+                for i, (r, _, _) in enumerate(group):
+                    r.cells = solver.member_cells[i]
+                active.append(_Slot(solver, [r for r, _, _ in group], head.steps, nb))
+                self.peak_used = max(self.peak_used, used)
+                self.peak_active = max(self.peak_active, len(active))
+                busy = True
+            # queue the next chunk of every idle solve
+            for sl in active:
+                if sl.remaining > 0 and sl.solver.query():
+                    k = min(self.chunk, sl.remaining)
+                    sl.solver.step(k)
+                    sl.remaining -= k
+                    busy = True
+            # collect finished solves
+            for sl in list(active):
+                if sl.remaining == 0 and sl.solver.query():
+                    tnow = time.perf_counter() - t0
+                    for i, r in enumerate(sl.reqs):
+                        r.result, r.t, r.steps_done = sl.solver.member_read(i)
+                        r.finished = tnow
+                    sl.solver.close()
+                    used -= sl.bytes
+                    active.remove(sl)
+                    busy = True
+            if not busy:
+                time.sleep(0.0002)
+        return requests
+
+
+def c5_requests(n: int = 256, lo: float = 5e3, hi: float = 2e6, steps: int = 200, rate: float = 1.0,
+                seed: int = 0, classes: int = 8):
+    """The serving stream: Poisson arrivals (rate per second), sizes
+    log-uniform in [lo, hi] cells rounded to `classes` log-spaced geometry
+    classes per kind, half density-wave cubes (inviscid) and half sphere
+    shells at Re ~ U[100, 300]."""
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    arrivals -= arrivals[0]
+    grid = np.exp(np.linspace(math.log(lo), math.log(hi), classes))
+    reqs = []
+    for i in range(n):
+        cells = math.exp(rng.uniform(math.log(lo), math.log(hi)))
+        target = grid[np.argmin(np.abs(np.log(grid) - math.log(cells)))]
+        if rng.uniform() < 0.5:
+            size = max(4, int(round((target / 6) ** (1 / 3))))
+            reqs.append(Request(i, float(arrivals[i]), "density", size, steps, density_params()))
+        else:
+            size = max(3, int(round((target / (6 * 1.3)) ** (1 / 3))))
+            re = float(rng.uniform(100, 300))
+            reqs.append(Request(i, float(arrivals[i]), "sphere", size, steps, sphere_params(re)))
+    return reqs
+
+
+def summarize(reqs):
+    lat = np.array([r.finished - r.arrival for r in reqs])
+    work = sum(r.cells * r.steps_done for r in reqs)
+    span = max(r.finished for r in reqs) - min(r.arrival for r in reqs)
+    return {"requests": len(reqs), "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(lat.mean()), "makespan_s": float(span), "cell_updates_per_s": work / span}
