@@ -74,9 +74,12 @@ struct Carver {
   }
 };
 
+// Uploads are queued on the solver's own stream, so that every later kernel
+// on that (non-blocking) stream is ordered after them; the host arrays stay
+// alive until the stream is synchronised at the end of solver creation.
 template <typename T>
-cudaError_t up(T* dst, const std::vector<T>& src) {
-  return cudaMemcpy(dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
+cudaError_t up(T* dst, const std::vector<T>& src, cudaStream_t st) {
+  return cudaMemcpyAsync(dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, st);
 }
 
 int check_params(const hgks_params* p) {
@@ -333,29 +336,29 @@ int create_solver(hgks_mesh* const* meshes, int n, const hgks_params* params, co
   dm.cmesh = p_cmesh;
   cudaError_t ue = cudaSuccess;
   auto chk = [&](cudaError_t x) { if (ue == cudaSuccess) ue = x; };
-  chk(up(p_volinv, volinv));
-  chk(up(p_hdt, m.hdt));
-  chk(up(p_hinv, m.hinv));
-  chk(up(p_mom, m.mom));
-  chk(up(p_sten, m.sten));
-  chk(up(p_pinv0, m.pinv0));
-  chk(up(p_subidx, m.subidx));
-  chk(up(p_pinvm, m.pinvm));
-  chk(up(p_cface, m.cface));
+  chk(up(p_volinv, volinv, s->stream));
+  chk(up(p_hdt, m.hdt, s->stream));
+  chk(up(p_hinv, m.hinv, s->stream));
+  chk(up(p_mom, m.mom, s->stream));
+  chk(up(p_sten, m.sten, s->stream));
+  chk(up(p_pinv0, m.pinv0, s->stream));
+  chk(up(p_subidx, m.subidx, s->stream));
+  chk(up(p_pinvm, m.pinvm, s->stream));
+  chk(up(p_cface, m.cface, s->stream));
   if (m.ng) {
-    chk(up(p_gsrc, m.gsrc));
-    chk(up(p_gtag, m.gtag));
-    chk(up(p_gnrm, m.gnrm));
+    chk(up(p_gsrc, m.gsrc, s->stream));
+    chk(up(p_gtag, m.gtag, s->stream));
+    chk(up(p_gnrm, m.gnrm, s->stream));
   }
-  chk(up(p_fown, m.fown));
-  chk(up(p_fnbr, m.fnbr));
-  chk(up(p_fdl, m.fdl));
-  chk(up(p_fdr, m.fdr));
-  chk(up(p_fn, m.fn));
-  chk(up(p_fw, m.fw));
-  if (p_cmesh) chk(up(p_cmesh, cmesh));
-  chk(cudaMemset(w.Q, 0, sizeof(double) * 5 * dm.nce));
-  chk(cudaMemset(w.Qs, 0, sizeof(double) * 5 * dm.nce));
+  chk(up(p_fown, m.fown, s->stream));
+  chk(up(p_fnbr, m.fnbr, s->stream));
+  chk(up(p_fdl, m.fdl, s->stream));
+  chk(up(p_fdr, m.fdr, s->stream));
+  chk(up(p_fn, m.fn, s->stream));
+  chk(up(p_fw, m.fw, s->stream));
+  if (p_cmesh) chk(up(p_cmesh, cmesh, s->stream));
+  chk(cudaMemsetAsync(w.Q, 0, sizeof(double) * 5 * dm.nce, s->stream));
+  chk(cudaMemsetAsync(w.Qs, 0, sizeof(double) * 5 * dm.nce, s->stream));
   if (ue != cudaSuccess) { cuda_fail(ue, "uploading the mesh"); return bail(HGKS_ECUDA); }
   // parameters
   hgks::DevParams& dp = s->dp;

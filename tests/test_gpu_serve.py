@@ -57,3 +57,22 @@ def test_admission_waits_for_memory():
     assert server.peak_used <= budget
     # some request was admitted only after another had finished and freed memory
     assert any(b.admitted >= a.finished for a in reqs for b in reqs if a is not b)
+
+
+def test_solver_creation_is_ordered_while_the_gpu_is_busy():
+    """A solver created while another solve keeps the GPU busy starts from
+    exactly its initial state (its uploads are ordered on its own stream)."""
+    from paper_2407_00656_b300 import inputs as I
+
+    xyz, cells, per = I.kuhn_cube(32, jitter=0.15, seed=0)
+    big = H.Solver(H.Mesh(xyz, cells, per), I.density_wave_state(xyz, cells, 0.0))
+    big.step(60)  # tens of ms of queued FP64 work on another stream
+    for n in (4, 5, 6):
+        x2, c2, p2 = I.kuhn_cube(n, jitter=0.15, seed=n)
+        q = I.random_smooth_state(x2, c2, seed=n)
+        small = H.Solver(H.Mesh(x2, c2, p2), q, precision=H.HGKS_FP32_MIXED)
+        got, t, k = small.read()
+        assert k == 0 and t == 0.0
+        assert np.array_equal(got, q)
+        small.close()
+    big.sync()
