@@ -39,7 +39,7 @@ FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12  # SMs x DFMA/clk x 2 flop x max
 def workload(name: str):
     from paper_2407_00656_b300 import inputs as I
 
-    if name in ("density48", "density24", "density12", "density8"):
+    if name.startswith("density") and name[len("density"):].isdigit():
         n = int(name[len("density"):])
         jit = 0.15 if n != 8 else 0.0
         xyz, cells, per = I.kuhn_cube(n, jitter=jit, seed=0)
