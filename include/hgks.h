@@ -87,10 +87,16 @@ typedef struct {
  *   precision      HGKS_FP64, or HGKS_FP32_MIXED: reconstruction and flux
  *                  in binary32, geometry, inverses and S2O4 in binary64.
  *   use_graph      1: replay each step as one captured CUDA graph.
- *   autotune       1: at hgks_init, time the kernel variants (register-capped
- *                  or uncapped flux; reconstruction rows staged by bulk
- *                  asynchronous copies or read directly) on this mesh and
- *                  keep the fastest.  All variants give bitwise equal results.
+ *   autotune       1: at hgks_init, time the kernel variants (flux with one
+ *                  thread per face or one per Gauss point; reconstruction
+ *                  rows staged by bulk asynchronous copies or read directly)
+ *                  on this mesh and keep the fastest.  The variants perform
+ *                  the same operations in the same order; in FP64 they give
+ *                  bitwise equal results, in FP32_MIXED they agree to within
+ *                  binary32 rounding (the compiler may schedule binary32
+ *                  operations differently per variant).  0: the defaults,
+ *                  flux per face in FP64 and per Gauss point in FP32_MIXED,
+ *                  rows staged.
  *   stream         cudaStream_t to run on, or NULL for a library stream. */
 typedef struct {
   double gamma, mu_ref, T_ref, visc_exp, Pr, cfl, tau_num_c, weno_eps, weno_gamma_lin;
@@ -164,8 +170,9 @@ int hgks_member_read(hgks_solver* s, int member, double* q_out, double* t_out, i
  * is still running, a negative code on error. */
 int hgks_query(hgks_solver* s);
 
-/* Kernel variants in use (see hgks_params.autotune): flux_variant 0
- * uncapped / 1 register-capped; recon_variant 0 staged / 1 direct. */
+/* Kernel variants in use (see hgks_params.autotune): flux_variant 0 one
+ * thread per face / 1 one thread per Gauss point; recon_variant 0 staged /
+ * 1 direct. */
 int hgks_tuning(const hgks_solver* s, int* flux_variant, int* recon_variant);
 /* Select the variants by hand (0 or 1 each); synchronises. */
 int hgks_set_tuning(hgks_solver* s, int flux_variant, int recon_variant);

@@ -374,7 +374,8 @@ int create_solver(hgks_mesh* const* meshes, int n, const hgks_params* params, co
   dp.glin = params->weno_gamma_lin;
   for (int i = 0; i < 5; ++i) dp.qinf[i] = params->q_inf[i];
   dp.viscous = (params->mu_ref > 0.0 || params->tau_num_c > 0.0) ? 1 : 0;
-  dp.flux_variant = 0;
+  hgks::fill_float_params(dp);
+  dp.flux_variant = s->precision == HGKS_FP32_MIXED ? 1 : 0;
   dp.recon_variant = 0;
   hgks::prepare_kernels(dm, s->precision);
   // initial states

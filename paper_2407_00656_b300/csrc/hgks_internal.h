@@ -40,11 +40,34 @@ struct DevMesh {
 struct DevParams {
   double gamma, Kint, mu_ref, T_ref, visc_exp, Pr, cfl, tau_c, eps, glin;
   double qinf[5];
+  double kq, kqi;  // (K+3)/4 and its reciprocal
+  // binary32 copies, rounded on the host, for the mixed-precision kernels
+  // (keeps binary64 -> binary32 conversions off the device's FP64 pipe)
+  float f_gamma, f_Kint, f_kq, f_kqi, f_mu_ref, f_T_ref, f_visc_exp, f_Pr, f_tau_c, f_eps, f_glin;
+  float f_qinf[5];
   int viscous;  // 1 when mu_ref > 0 or tau_c > 0 (collision time may be non-zero)
-  // kernel variants chosen by the autotuner (results are bitwise identical):
-  int flux_variant;   // 0: registers uncapped, 1: capped for 4 blocks of 128 per SM
+  // kernel variants chosen by the autotuner:
+  int flux_variant;   // 0: one thread per face, 1: one thread per Gauss point
   int recon_variant;  // 0: rows staged by bulk async copies, 1: rows read directly
 };
+
+// Fill kq, kqi and the binary32 copies of the parameters.
+inline void fill_float_params(DevParams& p) {
+  p.kq = 0.25 * (p.Kint + 3.0);
+  p.kqi = 4.0 / (p.Kint + 3.0);
+  p.f_gamma = (float)p.gamma;
+  p.f_Kint = (float)p.Kint;
+  p.f_kq = (float)(0.25 * (p.Kint + 3.0));
+  p.f_kqi = (float)(4.0 / (p.Kint + 3.0));
+  p.f_mu_ref = (float)p.mu_ref;
+  p.f_T_ref = (float)p.T_ref;
+  p.f_visc_exp = (float)p.visc_exp;
+  p.f_Pr = (float)p.Pr;
+  p.f_tau_c = (float)p.tau_c;
+  p.f_eps = (float)p.eps;
+  p.f_glin = (float)p.glin;
+  for (int i = 0; i < 5; ++i) p.f_qinf[i] = (float)p.qinf[i];
+}
 
 // Step control block in device memory.
 struct Control {

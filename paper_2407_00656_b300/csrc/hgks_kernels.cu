@@ -55,6 +55,14 @@ __device__ __forceinline__ float cvt<float>(double x) {
   return __uint_as_float(e < 897u ? sign : r);
 }
 
+// A parameter in the kernel's precision: the binary64 value or its copy
+// rounded to binary32 on the host.
+template <typename Real>
+__device__ __forceinline__ Real pick(double d, float f) {
+  if constexpr (sizeof(Real) == 4) return f;
+  else return d;
+}
+
 // --------------------------------------------------------------------------
 // Maxwellian moments.  Mom holds normalised one-dimensional moments <u^k>,
 // <v^k>, <w^k> and <(xi^2)^k> of one Maxwellian (u possibly on a half-line).
@@ -118,17 +126,21 @@ __device__ __forceinline__ Prim<R> prim_of(const R q[5], R kq, R kqi) {
 }
 
 // Moments of a Maxwellian; half = +1: u > 0, -1: u < 0, 0: full line.
+// Eh receives half * exp(-lam U^2)/(2 sqrt(pi lam)), the boundary term of the
+// half-line recursion (0 on the full line).
 template <int NU, typename R>
-__device__ __forceinline__ void moments(const Prim<R>& p, int half, R Kint, Mom<R>& M) {
+__device__ __forceinline__ void moments(const Prim<R>& p, int half, R Kint, Mom<R>& M, R& Eh) {
   if (half == 0) {
     M.u[0] = R(1);
     M.u[1] = p.U;
+    Eh = R(0);
   } else {
     const R rs = rsqrt(p.lam);
     const R s = R(half) * p.lam * rs * p.U;  // sqrt(lam) U
     const R e = exp(-p.lam * p.U * p.U) * R(0.28209479177387814) * rs;  // exp(-lam U^2)/(2 sqrt(pi lam))
     M.u[0] = R(0.5) * erfc(-s);
-    M.u[1] = p.U * M.u[0] + R(half) * e;
+    Eh = R(half) * e;
+    M.u[1] = p.U * M.u[0] + Eh;
   }
   recur<NU>(M.u, p.U, p.h2);
   M.v[0] = R(1);
@@ -189,10 +201,74 @@ __device__ __forceinline__ void euler_jv(const EState<R>& s, const R d[5], R o[5
   o[4] = (d[4] + dp) * s.u[j] + (s.E + s.p) * duj;
 }
 
+// Half-space contribution c = rho <psi>^sigma of one side to the interface
+// equilibrium Q0 (Section 2.1), and its derivatives dc[j] along the local
+// axes for the conservative-variable derivatives dq[j].
+//
+// By the definition of the micro-slope (g_x = a g), the term int psi a_j g
+// over the half-line of Q0's slope equals d/dx_j of rho <psi>^sigma, and
+// rho <psi>^sigma is a closed-form function of (rho, U, V, W, lam):
+//   c = rho (u0, u1, u0 V, u0 W, (u2 + u0 S)/2),  S = V^2 + W^2 + (K+2)/(2 lam),
+// with u_n the half-line moments of the normal velocity.  Their parameter
+// derivatives follow from differentiating under the integral and the
+// half-line recursion (E = half-line boundary term):
+//   du0/dU = 2 lam E,  du0/dlam = U E,
+//   du1/dU = u0,       du1/dlam = -E/(2 lam),
+//   du2/dU = 2 u1,     du2/dlam = -u0/(2 lam^2).
+// The chain rule through the primitive variables then gives dc without the
+// half-space Gram matrix or the micro-slopes.  Quantities rho dU, rho dV,
+// rho dW and rho dlam are formed directly from dq.
+template <typename R>
+__device__ __forceinline__ void half_jet(const Prim<R>& p, R u0, R u1, R Eh, R Kint, R kqi, const R dq[3][5],
+                                         R c[5], R dc[3][5]) {
+  const R h2 = p.h2;
+  const R u2 = p.U * u1 + h2 * u0;
+  const R S = p.V * p.V + p.W * p.W + (Kint + R(2)) * h2;
+  c[0] = p.rho * u0;
+  c[1] = p.rho * u1;
+  c[2] = c[0] * p.V;
+  c[3] = c[0] * p.W;
+  c[4] = R(0.5) * p.rho * (u2 + u0 * S);
+  const R tl = R(2) * p.lam, lk = p.lam * kqi, hU2 = R(0.5) * (p.U * p.U + p.V * p.V + p.W * p.W);
+  const R hE = h2 * Eh, h22u0 = R(2) * h2 * h2 * u0, kS = R(2) * (Kint + R(2)) * h2 * h2;
+  const R a2 = u2 + u0 * S;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const R* d = dq[j];
+    const R PU = d[1] - p.U * d[0], PV = d[2] - p.V * d[0], PW = d[3] - p.W * d[0];
+    const R de = d[4] - p.U * d[1] - p.V * d[2] - p.W * d[3] + hU2 * d[0];  // d(rho e_int)
+    const R Pl = p.lam * (d[0] - lk * de);                                  // rho dlam
+    const R rdu0 = Eh * (tl * PU + p.U * Pl);
+    const R rdu1 = u0 * PU - hE * Pl;
+    const R rdu2 = R(2) * u1 * PU - h22u0 * Pl;
+    const R rdS = R(2) * (p.V * PV + p.W * PW) - kS * Pl;
+    const R d0 = d[0] * u0 + rdu0;
+    dc[j][0] = d0;
+    dc[j][1] = d[0] * u1 + rdu1;
+    dc[j][2] = p.V * d0 + u0 * PV;
+    dc[j][3] = p.W * d0 + u0 * PW;
+    dc[j][4] = R(0.5) * (d[0] * a2 + rdu2 + S * rdu0 + u0 * rdS);
+  }
+}
+
 template <typename R>
 struct FluxParams {
   R gamma, Kint, kq, kqi, mu_ref, T_ref, visc_exp, Pr, tau_c;  // kq = (K+3)/4, kqi = 1/kq
 };
+template <typename R>
+__device__ __forceinline__ FluxParams<R> flux_params(const DevParams& P) {
+  FluxParams<R> F;
+  F.gamma = pick<R>(P.gamma, P.f_gamma);
+  F.Kint = pick<R>(P.Kint, P.f_Kint);
+  F.kq = pick<R>(P.kq, P.f_kq);
+  F.kqi = pick<R>(P.kqi, P.f_kqi);
+  F.mu_ref = pick<R>(P.mu_ref, P.f_mu_ref);
+  F.T_ref = pick<R>(P.T_ref, P.f_T_ref);
+  F.visc_exp = pick<R>(P.visc_exp, P.f_visc_exp);
+  F.Pr = pick<R>(P.Pr, P.f_Pr);
+  F.tau_c = pick<R>(P.tau_c, P.f_tau_c);
+  return F;
+}
 
 // <u psi_i P> for P = a.u (a_j micro-slopes along x, y, z, rho-weighted),
 // expanded into the twelve monomials of P.
@@ -221,41 +297,24 @@ __device__ void gks_flux(const R ql[5], const R dl[3][5], const R qr[5], const R
                          const FluxParams<R>& P, R F[5], R dF[5]) {
   const R K = P.Kint;
   const Prim<R> pl = prim_of(ql, P.kq, P.kqi), pr = prim_of(qr, P.kq, P.kqi);
-  constexpr int NU = VISC ? 7 : 5;
+  constexpr int NU = VISC ? 7 : 3;
   Mom<R> Ml, Mr;
-  moments<NU>(pl, +1, K, Ml);
-  moments<NU>(pr, -1, K, Mr);
+  R El, Er;
+  moments<NU>(pl, +1, K, Ml, El);
+  moments<NU>(pr, -1, K, Mr, Er);
 
-  // half-space Gram matrices <psi_i psi_j>^(+/-), symmetric
-  R Gl[5][5], Gr[5][5];
-  sfor<5>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    sfor<5>([&](auto J) {
-      constexpr int j = decltype(J)::value;
-      if constexpr (j >= i) {
-        Gl[i][j] = Gl[j][i] = mpsi2<i, j, 0, 0, 0>(Ml);
-        Gr[i][j] = Gr[j][i] = mpsi2<i, j, 0, 0, 0>(Mr);
-      }
-    });
-  });
-  // interface equilibrium Q0 = rho_l <psi>^+_l + rho_r <psi>^-_r
-  R q0[5];
-#pragma unroll
-  for (int i = 0; i < 5; ++i) q0[i] = pl.rho * Gl[0][i] + pr.rho * Gr[0][i];
-
-  // dQ0/dn_j = int_{u>0} psi a^l_j g_l + int_{u<0} psi a^r_j g_r
-  R dq0[3][5];
-  R al[3][5], ar[3][5];
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    micro_slope_rho(pl, P.kq, P.kqi, dl[j], al[j]);  // rho_l a^l_j
-    micro_slope_rho(pr, P.kq, P.kqi, dr[j], ar[j]);
+  // interface equilibrium Q0 = rho_l <psi>^+_l + rho_r <psi>^-_r and its
+  // slopes dQ0/dn_j = int_{u>0} psi a^l_j g_l + int_{u<0} psi a^r_j g_r
+  R q0[5], dq0[3][5];
+  {
+    R cl[5], dcl[3][5], cr[5], dcr[3][5];
+    half_jet(pl, Ml.u[0], Ml.u[1], El, K, P.kqi, dl, cl, dcl);
+    half_jet(pr, Mr.u[0], Mr.u[1], Er, K, P.kqi, dr, cr, dcr);
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
-      R s = R(0);
+      q0[i] = cl[i] + cr[i];
 #pragma unroll
-      for (int k = 0; k < 5; ++k) s += Gl[i][k] * al[j][k] + Gr[i][k] * ar[j][k];
-      dq0[j][i] = s;
+      for (int j = 0; j < 3; ++j) dq0[j][i] = dcl[j][i] + dcr[j][i];
     }
   }
   // Euler flux of Q0 and the time derivative of Q0 from the compatibility
@@ -296,7 +355,8 @@ __device__ void gks_flux(const R ql[5], const R dl[3][5], const R qr[5], const R
 #pragma unroll
     for (int j = 0; j < 3; ++j) micro_slope_rho(p0, P.kq, P.kqi, dq0[j], ab[j]);
     Mom<R> M0;
-    moments<7>(p0, 0, K, M0);
+    R E0;
+    moments<7>(p0, 0, K, M0, E0);
     R X0[5];
     flux_of_slope(M0, ab, X0);  // rho0 <u (abar.u) psi>
     // side terms: rho_k A^k from <a^k.u + A^k> = 0, full-space moments of g_k
@@ -316,6 +376,12 @@ __device__ void gks_flux(const R ql[5], const R dl[3][5], const R qr[5], const R
 #pragma unroll
       for (int i = 0; i < 5; ++i) tmp[i] = -(tmp[i] + s1[i] + s2[i]);
       micro_slope_rho(pr, P.kq, P.kqi, tmp, Ar);
+    }
+    R al[3][5], ar[3][5];  // rho_k a^k_j
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      micro_slope_rho(pl, P.kq, P.kqi, dl[j], al[j]);
+      micro_slope_rho(pr, P.kq, P.kqi, dr[j], ar[j]);
     }
     R Xl[5], Xr[5], Nk[5], Yk[5];
     flux_of_slope(Ml, al, Xl);
@@ -774,7 +840,7 @@ __global__ void __launch_bounds__(kRThreads) k_recon(DevMesh m, DevParams P, con
 #pragma unroll
   for (int q = 0; q < 6; ++q) mi[q] = cvt<Real>(m.mom[q * nc + c]);
   const Real hi = cvt<Real>(m.hinv[c]);
-  const Real glin = (Real)P.glin, g0 = Real(1) - Real(M) * glin, eps = (Real)P.eps;
+  const Real glin = pick<Real>(P.glin, P.f_glin), g0 = Real(1) - Real(M) * glin, eps = pick<Real>(P.eps, P.f_eps);
   recon_finish<Real, M>(a, b, qv, mi, hi, glin, g0, eps, coef + (int64_t)v * 10 * nc + c, nc);
 }
 
@@ -797,120 +863,157 @@ __device__ __forceinline__ void eval_poly(const Real* __restrict__ coef, int64_t
   }
 }
 
-// Face flux, one thread per face: sum over the Gauss points of weight*area
-// times the flux of Eq. (flux), F and dF/dt in the global frame, oriented
-// from the owner to the neighbour.  Output Fs[j*nf + f], j = 0..4 F, 5..9 dF.
-template <typename Real, int G, bool VISC, int MINB>
-__global__ void __launch_bounds__(kBlock, MINB) k_flux(DevMesh m, DevParams P, const Real* __restrict__ coef,
-                                                       Real* __restrict__ Fs, const Control* __restrict__ ctl) {
+// Flux of Gauss point g of face f (Eq. flux at one point of the face
+// quadrature), rotated back to the global frame and oriented from the owner
+// to the neighbour: r[0..4] = F, r[5..9] = dF/dt.  Returns the point's
+// quadrature weight times area.
+template <typename Real, int G, bool VISC>
+__device__ __forceinline__ Real point_flux(const DevMesh& m, const DevParams& P, const FluxParams<Real>& FP,
+                                           const Real* __restrict__ coef, int64_t f, int g, int64_t own, int nbr,
+                                           Real dt, Real r[10]) {
   const int64_t nf = m.nf, nc = m.nc;
+  // planar triangles share one normal; bilinear quads have one per point
+  Real n[3], t1[3], t2[3];
+  const int gn = G == 3 ? 0 : g;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) n[a] = cvt<Real>(m.fn[(gn * 3 + a) * nf + f]);
+  frame(n, t1, t2);
+  Real d[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) d[a] = cvt<Real>(m.fdl[(g * 3 + a) * nf + f]);
+  const Real wgt = cvt<Real>(m.fw[g * nf + f]);
+  Real qv[5], gr[5][3];
+  eval_poly(coef, nc, own, d, qv, gr);
+  // local frame: rotate momentum, take derivatives along n, t1, t2
+  Real ql[5], dl[3][5], qr[5], dr[3][5];
+  auto rot = [&](const Real x[5], Real y[5]) {
+    y[0] = x[0];
+    y[1] = x[1] * n[0] + x[2] * n[1] + x[3] * n[2];
+    y[2] = x[1] * t1[0] + x[2] * t1[1] + x[3] * t1[2];
+    y[3] = x[1] * t2[0] + x[2] * t2[1] + x[3] * t2[2];
+    y[4] = x[4];
+  };
+  auto local = [&](const Real q[5], const Real gg[5][3], Real qo[5], Real dd[3][5]) {
+    rot(q, qo);
+    Real tmp[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) tmp[v] = gg[v][0] * n[0] + gg[v][1] * n[1] + gg[v][2] * n[2];
+    rot(tmp, dd[0]);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) tmp[v] = gg[v][0] * t1[0] + gg[v][1] * t1[1] + gg[v][2] * t1[2];
+    rot(tmp, dd[1]);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) tmp[v] = gg[v][0] * t2[0] + gg[v][1] * t2[1] + gg[v][2] * t2[2];
+    rot(tmp, dd[2]);
+  };
+  local(qv, gr, ql, dl);
+  if (nbr >= 0) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d[a] = cvt<Real>(m.fdr[(g * 3 + a) * nf + f]);
+    eval_poly(coef, nc, (int64_t)nbr, d, qv, gr);
+    local(qv, gr, qr, dr);
+  } else if (nbr == -3) {
+    // no-slip adiabatic wall: mirror state, momentum reversed, normal
+    // derivative reflected
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const Real sg = (v >= 1 && v <= 3) ? Real(-1) : Real(1);
+      qr[v] = sg * ql[v];
+      dr[0][v] = -sg * dl[0][v];
+      dr[1][v] = sg * dl[1][v];
+      dr[2][v] = sg * dl[2][v];
+    }
+  } else {
+    // Riemann-invariant far field, evaluated in the local frame, zero gradient
+    Real qinf[5], qil[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) qinf[v] = pick<Real>(P.qinf[v], P.f_qinf[v]);
+    rot(qinf, qil);
+    const Real ex[3] = {Real(1), Real(0), Real(0)};
+    farfield(ql, qil, ex, FP.gamma, qr);
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int v = 0; v < 5; ++v) dr[j][v] = Real(0);
+  }
+  Real Fl[5], Dl[5];
+  gks_flux<Real, VISC>(ql, dl, qr, dr, dt, FP, Fl, Dl);
+  // back to the global frame
+  r[0] = Fl[0];
+  r[4] = Fl[4];
+  r[5] = Dl[0];
+  r[9] = Dl[4];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    r[1 + a] = fma(Fl[1], n[a], fma(Fl[2], t1[a], Fl[3] * t2[a]));
+    r[6 + a] = fma(Dl[1], n[a], fma(Dl[2], t1[a], Dl[3] * t2[a]));
+  }
+  return wgt;
+}
+
+// Face flux, one thread per face: sum over the Gauss points of weight*area
+// times the point flux.  Output Fs[j*nf + f], j = 0..4 F, 5..9 dF.
+template <typename Real, int G, bool VISC>
+__global__ void __launch_bounds__(kBlock) k_flux(DevMesh m, DevParams P, const Real* __restrict__ coef,
+                                                 Real* __restrict__ Fs, const Control* __restrict__ ctl) {
+  const int64_t nf = m.nf;
   const int64_t f = (int64_t)blockIdx.x * kBlock + threadIdx.x;
   if (f >= nf) return;
-  const double dtd = ctl[member_of(m, m.fown[f])].dt;
-  if (dtd == 0.0) return;
-  const Real dt = (Real)dtd;
-  FluxParams<Real> FP;
-  FP.gamma = (Real)P.gamma;
-  FP.Kint = (Real)P.Kint;
-  FP.kq = (Real)(0.25 * (P.Kint + 3.0));
-  FP.kqi = (Real)(4.0 / (P.Kint + 3.0));
-  FP.mu_ref = (Real)P.mu_ref;
-  FP.T_ref = (Real)P.T_ref;
-  FP.visc_exp = (Real)P.visc_exp;
-  FP.Pr = (Real)P.Pr;
-  FP.tau_c = (Real)P.tau_c;
   const int64_t own = m.fown[f];
+  const double dtd = ctl[member_of(m, own)].dt;
+  if (dtd == 0.0) return;
+  const Real dt = cvt<Real>(dtd);
+  const FluxParams<Real> FP = flux_params<Real>(P);
   const int nbr = m.fnbr[f];
-  Real Fa[5] = {0, 0, 0, 0, 0}, Da[5] = {0, 0, 0, 0, 0};
-  // planar triangles share one normal and frame; bilinear quads have one per point
-  Real n[3], t1[3], t2[3];
-  if constexpr (G == 3) {
+  Real acc[10];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) n[a] = cvt<Real>(m.fn[a * nf + f]);
-    frame(n, t1, t2);
-  }
+  for (int v = 0; v < 10; ++v) acc[v] = Real(0);
 #pragma unroll 1
   for (int g = 0; g < G; ++g) {
-    Real d[3];
+    Real r[10];
+    const Real w = point_flux<Real, G, VISC>(m, P, FP, coef, f, g, own, nbr, dt, r);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) d[a] = cvt<Real>(m.fdl[(g * 3 + a) * nf + f]);
-    if constexpr (G != 3) {
-#pragma unroll
-      for (int a = 0; a < 3; ++a) n[a] = cvt<Real>(m.fn[(g * 3 + a) * nf + f]);
-      frame(n, t1, t2);
-    }
-    const Real wgt = cvt<Real>(m.fw[g * nf + f]);
-    Real qv[5], gr[5][3];
-    eval_poly(coef, nc, own, d, qv, gr);
-    // local frame: rotate momentum, take derivatives along n, t1, t2
-    Real ql[5], dl[3][5], qr[5], dr[3][5];
-    auto rot = [&](const Real x[5], Real y[5]) {
-      y[0] = x[0];
-      y[1] = x[1] * n[0] + x[2] * n[1] + x[3] * n[2];
-      y[2] = x[1] * t1[0] + x[2] * t1[1] + x[3] * t1[2];
-      y[3] = x[1] * t2[0] + x[2] * t2[1] + x[3] * t2[2];
-      y[4] = x[4];
-    };
-    auto local = [&](const Real q[5], const Real gg[5][3], Real qo[5], Real dd[3][5]) {
-      rot(q, qo);
-      Real tmp[5];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) tmp[v] = gg[v][0] * n[0] + gg[v][1] * n[1] + gg[v][2] * n[2];
-      rot(tmp, dd[0]);
-#pragma unroll
-      for (int v = 0; v < 5; ++v) tmp[v] = gg[v][0] * t1[0] + gg[v][1] * t1[1] + gg[v][2] * t1[2];
-      rot(tmp, dd[1]);
-#pragma unroll
-      for (int v = 0; v < 5; ++v) tmp[v] = gg[v][0] * t2[0] + gg[v][1] * t2[1] + gg[v][2] * t2[2];
-      rot(tmp, dd[2]);
-    };
-    local(qv, gr, ql, dl);
-    if (nbr >= 0) {
-#pragma unroll
-      for (int a = 0; a < 3; ++a) d[a] = cvt<Real>(m.fdr[(g * 3 + a) * nf + f]);
-      eval_poly(coef, nc, (int64_t)nbr, d, qv, gr);
-      local(qv, gr, qr, dr);
-    } else if (nbr == -3) {
-      // no-slip adiabatic wall: mirror state, momentum reversed, normal
-      // derivative reflected
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        const Real sg = (v >= 1 && v <= 3) ? Real(-1) : Real(1);
-        qr[v] = sg * ql[v];
-        dr[0][v] = -sg * dl[0][v];
-        dr[1][v] = sg * dl[1][v];
-        dr[2][v] = sg * dl[2][v];
-      }
-    } else {
-      // Riemann-invariant far field, evaluated in the local frame, zero gradient
-      Real qinf[5], qil[5];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) qinf[v] = (Real)P.qinf[v];
-      rot(qinf, qil);
-      const Real ex[3] = {Real(1), Real(0), Real(0)};
-      farfield(ql, qil, ex, FP.gamma, qr);
-#pragma unroll
-      for (int j = 0; j < 3; ++j)
-#pragma unroll
-        for (int v = 0; v < 5; ++v) dr[j][v] = Real(0);
-    }
-    Real Fl[5], Dl[5];
-    gks_flux<Real, VISC>(ql, dl, qr, dr, dt, FP, Fl, Dl);
-    // back to the global frame, weighted by the quadrature weight times area
-    Fa[0] += wgt * Fl[0];
-    Da[0] += wgt * Dl[0];
-    Fa[4] += wgt * Fl[4];
-    Da[4] += wgt * Dl[4];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      Fa[1 + a] += wgt * (Fl[1] * n[a] + Fl[2] * t1[a] + Fl[3] * t2[a]);
-      Da[1 + a] += wgt * (Dl[1] * n[a] + Dl[2] * t1[a] + Dl[3] * t2[a]);
-    }
+    for (int v = 0; v < 10; ++v) acc[v] = fma(w, r[v], acc[v]);
   }
 #pragma unroll
-  for (int v = 0; v < 5; ++v) {
-    Fs[v * nf + f] = Fa[v];
-    Fs[(5 + v) * nf + f] = Da[v];
+  for (int v = 0; v < 10; ++v) Fs[v * nf + f] = acc[v];
+}
+
+// Face flux, one thread per Gauss point: the G points of a face run on G
+// threads (kBlock / G faces per block), so each thread holds one point's
+// state, and the block sums the points of each face in shared memory with
+// the same fused multiply-adds, in the same order, as k_flux.
+template <typename Real, int G, bool VISC, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_flux_gp(DevMesh m, DevParams P, const Real* __restrict__ coef,
+                                                          Real* __restrict__ Fs, const Control* __restrict__ ctl) {
+  constexpr int FB = kBlock / G;  // faces per block
+  __shared__ Real sr[G][10][FB];
+  __shared__ Real sw[G][FB];
+  const int64_t nf = m.nf;
+  const int gp = threadIdx.x / FB, fl = threadIdx.x - gp * FB;
+  const int64_t f0 = (int64_t)blockIdx.x * FB;
+  const int64_t f = f0 + fl;
+  if (gp < G && f < nf) {
+    const int64_t own = m.fown[f];
+    const double dtd = ctl[member_of(m, own)].dt;
+    Real r[10], w = Real(0);
+#pragma unroll
+    for (int v = 0; v < 10; ++v) r[v] = Real(0);
+    if (dtd != 0.0)
+      w = point_flux<Real, G, VISC>(m, P, flux_params<Real>(P), coef, f, gp, own, m.fnbr[f], cvt<Real>(dtd), r);
+    sw[gp][fl] = w;
+#pragma unroll
+    for (int v = 0; v < 10; ++v) sr[gp][v][fl] = r[v];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 10 * FB; e += kBlock) {
+    const int v = e / FB, l = e - v * FB;
+    const int64_t ff = f0 + l;
+    if (ff >= nf) continue;
+    Real acc = Real(0);
+#pragma unroll
+    for (int g = 0; g < G; ++g) acc = fma(sw[g][l], sr[g][v][l], acc);
+    Fs[v * nf + ff] = acc;
   }
 }
 
@@ -1066,9 +1169,14 @@ void recon_any(const DevMesh& m, const DevParams& p, const QT* Q, Real* coef, Co
 
 template <typename Real, int G, bool VISC>
 void flux_launch(const DevMesh& m, const DevParams& p, const Real* coef, Real* Fs, const Control* ctl, cudaStream_t s) {
-  const unsigned nb = blocks(m.nf);
-  if (p.flux_variant == 1) k_flux<Real, G, VISC, 4><<<nb, kBlock, 0, s>>>(m, p, coef, Fs, ctl);
-  else k_flux<Real, G, VISC, 1><<<nb, kBlock, 0, s>>>(m, p, coef, Fs, ctl);
+  if (p.flux_variant == 1) {
+    constexpr int FB = kBlock / G;
+    // binary32: 4 blocks of 128 per SM (128 registers); binary64: 2
+    k_flux_gp<Real, G, VISC, sizeof(Real) == 4 ? 4 : 2>
+        <<<(unsigned)((m.nf + FB - 1) / FB), kBlock, 0, s>>>(m, p, coef, Fs, ctl);
+  } else {
+    k_flux<Real, G, VISC><<<blocks(m.nf), kBlock, 0, s>>>(m, p, coef, Fs, ctl);
+  }
 }
 
 template <typename Real>
