@@ -39,20 +39,28 @@ FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12  # SMs x DFMA/clk x 2 flop x max
 def workload(name: str):
     from paper_2407_00656_b300 import inputs as I
 
-    if name.startswith("density") and name[len("density"):].isdigit():
-        n = int(name[len("density"):])
+    # densityN: the N^3 x 6 tet density wave, inviscid; densityNv: the same
+    # with constant viscosity mu = 1e-3, Pr = 0.72
+    body = name[len("density"):] if name.startswith("density") else ""
+    visc = body.endswith("v")
+    if body and body.rstrip("v").isdigit():
+        n = int(body.rstrip("v"))
         jit = 0.15 if n != 8 else 0.0
         xyz, cells, per = I.kuhn_cube(n, jitter=jit, seed=0)
         q = I.density_wave_state(xyz, cells, 0.0)
-        return dict(xyz=xyz, cells=cells, periods=per, q=q, params={},
-                    desc=f"density wave, {n}^3 x 6 tets" + (", jitter 0.15h seed 0" if jit else "") + ", inviscid")
-    if name == "sphere":
-        xyz, cells, bfn, bft = I.sphere_shell(58, 75, seed=0)
+        params = dict(mu_ref=1e-3, Pr=0.72, visc_exp=0.0, T_ref=1.0, tau_num_c=0.0) if visc else {}
+        return dict(xyz=xyz, cells=cells, periods=per, q=q, params=params,
+                    desc=f"density wave, {n}^3 x 6 tets" + (", jitter 0.15h seed 0" if jit else "") +
+                    (", mu 1e-3 Pr 0.72" if visc else ", inviscid"))
+    # sphere: the 1.51M-cell shell 6 x 58^2 x 75; sphereN: 6 x N^2 x round(1.3 N)
+    if name == "sphere" or (name.startswith("sphere") and name[len("sphere"):].isdigit()):
+        n, nr = (58, 75) if name == "sphere" else (int(name[len("sphere"):]), max(2, round(1.3 * int(name[len("sphere"):]))))
+        xyz, cells, bfn, bft = I.sphere_shell(n, nr, seed=0)
         qinf = I.free_stream(0.2535)
         q = np.tile(qinf, (len(cells), 1))
         return dict(xyz=xyz, cells=cells, periods=None, bfn=bfn, bft=bft, q=q,
                     params=dict(q_inf=qinf, mu_ref=0.2535 / 300, Pr=0.72, visc_exp=0.7, T_ref=1 / 1.4, tau_num_c=1.0),
-                    desc="sphere shell 6x58^2x75 hex, Ma 0.2535 Re 300, wall + far field")
+                    desc=f"sphere shell 6x{n}^2x{nr} hex, Ma 0.2535 Re 300, wall + far field")
     raise ValueError(name)
 
 
@@ -121,13 +129,18 @@ def cpu_baseline(w, budget_steps: int = 1):
 def run_reference(args, rank, world):
     """The CPU checker as it stands on the host cores (rank 0 only).  Each
     timed step is one S2O4 step of a bounded sample of the workload: the
-    24^3 x 6 jittered mesh for the density-wave workloads."""
+    24^3 x 6 jittered mesh for the density-wave workloads, the 6 x 24^2 x 31
+    shell for the sphere workloads."""
     if rank != 0:
         return
     import oracle
 
     w = workload(args.workload)
-    ws = workload("density24") if args.workload.startswith("density") else w
+    ws = w
+    if args.workload.startswith("density"):
+        ws = workload("density24v" if args.workload.endswith("v") else "density24")
+    elif args.workload.startswith("sphere"):
+        ws = workload("sphere24")
     cores = os.cpu_count() or 1
     oracle.set_threads(cores)
     o = oracle.Oracle(ws["xyz"], ws["cells"], ws["periods"], ws.get("bfn"), ws.get("bft"),

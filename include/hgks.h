@@ -91,12 +91,11 @@ typedef struct {
  *                  thread per face or one per Gauss point; reconstruction
  *                  rows staged by bulk asynchronous copies or read directly)
  *                  on this mesh and keep the fastest.  The variants perform
- *                  the same operations in the same order; in FP64 they give
- *                  bitwise equal results, in FP32_MIXED they agree to within
- *                  binary32 rounding (the compiler may schedule binary32
- *                  operations differently per variant).  0: the defaults,
- *                  flux per face in FP64 and per Gauss point in FP32_MIXED,
- *                  rows staged.
+ *                  the same operations in the same order and agree to a few
+ *                  units in the last place (the compiler may fuse a
+ *                  multiply and an add in one variant and not in another);
+ *                  each variant is deterministic.  0: the defaults, flux per
+ *                  Gauss point, rows staged.
  *   stream         cudaStream_t to run on, or NULL for a library stream. */
 typedef struct {
   double gamma, mu_ref, T_ref, visc_exp, Pr, cfl, tau_num_c, weno_eps, weno_gamma_lin;

@@ -88,7 +88,8 @@ struct DevWork {
   double* Q;      // [5][nce] state Q^n, ghost slots at [nc, nce)
   double* Qs;     // [5][nce] stage state Q*
   double* R;      // [5][nc]  Q^n + dt L^n + dt^2/6 dL^n
-  float* Qf;      // [5][nce] binary32 copy of the stage state (mixed precision only)
+  float* Qf;      // [nce][8] binary32 copy of the stage state, one 32-byte record per cell
+                  // (5 variables, 3 zero pads; mixed precision only)
   void* coef;     // [50][nc] reconstruction polynomials (double or float)
   void* Fs;       // [10][nf] face flux sums: F (5) then dF/dt (5) (double or float)
   Control* ctl;   // [nmesh] one control block per member mesh

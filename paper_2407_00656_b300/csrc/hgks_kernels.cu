@@ -55,6 +55,19 @@ __device__ __forceinline__ float cvt<float>(double x) {
   return __uint_as_float(e < 897u ? sign : r);
 }
 
+// The binary32 state copy holds one 32-byte record per cell (5 variables and
+// 3 zero pads), so one stencil gather fetches all five variables of a cell.
+__device__ __forceinline__ void store_qf(float* __restrict__ Qf, int64_t c, const double q[5]) {
+  float4* r = reinterpret_cast<float4*>(Qf + 8 * c);
+  r[0] = make_float4((float)q[0], (float)q[1], (float)q[2], (float)q[3]);
+  r[1] = make_float4((float)q[4], 0.f, 0.f, 0.f);
+}
+// Variable v of cell c of a state: binary64 [5][nce] or binary32 [nce][8].
+__device__ __forceinline__ double qget(const double* __restrict__ Q, int64_t nce, int v, int64_t c) {
+  return Q[v * nce + c];
+}
+__device__ __forceinline__ float qget(const float* __restrict__ Q, int64_t, int v, int64_t c) { return Q[8 * c + v]; }
+
 // A parameter in the kernel's precision: the binary64 value or its copy
 // rounded to binary32 on the host.
 template <typename Real>
@@ -71,31 +84,6 @@ template <typename R>
 struct Mom {
   R u[7], v[6], w[6], x[3];
 };
-
-template <int a, int b, int c, int d, typename R>
-__device__ __forceinline__ R mm(const Mom<R>& M) {
-  return M.u[a] * M.v[b] * M.w[c] * M.x[d];
-}
-// <u^a v^b w^c (xi^2)^d psi_i>, psi = (1, u, v, w, (u^2+v^2+w^2+xi^2)/2)
-template <int i, int a, int b, int c, int d, typename R>
-__device__ __forceinline__ R mpsi(const Mom<R>& M) {
-  if constexpr (i == 0) return mm<a, b, c, d>(M);
-  else if constexpr (i == 1) return mm<a + 1, b, c, d>(M);
-  else if constexpr (i == 2) return mm<a, b + 1, c, d>(M);
-  else if constexpr (i == 3) return mm<a, b, c + 1, d>(M);
-  else return R(0.5) * (mm<a + 2, b, c, d>(M) + mm<a, b + 2, c, d>(M) + mm<a, b, c + 2, d>(M) + mm<a, b, c, d + 1>(M));
-}
-// <u^a v^b w^c psi_i psi_j>
-template <int i, int j, int a, int b, int c, typename R>
-__device__ __forceinline__ R mpsi2(const Mom<R>& M) {
-  if constexpr (j == 0) return mpsi<i, a, b, c, 0>(M);
-  else if constexpr (j == 1) return mpsi<i, a + 1, b, c, 0>(M);
-  else if constexpr (j == 2) return mpsi<i, a, b + 1, c, 0>(M);
-  else if constexpr (j == 3) return mpsi<i, a, b, c + 1, 0>(M);
-  else
-    return R(0.5) * (mpsi<i, a + 2, b, c, 0>(M) + mpsi<i, a, b + 2, c, 0>(M) + mpsi<i, a, b, c + 2, 0>(M) +
-                     mpsi<i, a, b, c, 1>(M));
-}
 
 // Gaussian recursion <u^{n+2}> = U <u^{n+1}> + (n+1)/(2 lam) <u^n>
 template <int N, typename R>
@@ -152,23 +140,6 @@ __device__ __forceinline__ void moments(const Prim<R>& p, int half, R Kint, Mom<
   M.x[0] = R(1);
   M.x[1] = Kint * p.h2;                        // <xi^2> = K/(2 lam)
   M.x[2] = Kint * (Kint + R(2)) * p.h2 * p.h2;  // <xi^4> = K(K+2)/(4 lam^2)
-}
-
-// Micro-slope from a derivative dq of the conservative variables (Section
-// 2.1), in closed form: returns rho * a for the polynomial a(psi) with
-// rho <a psi> = dq under the Maxwellian p.
-template <typename R>
-__device__ __forceinline__ void micro_slope_rho(const Prim<R>& p, R kq, R kqi, const R dq[5], R a[5]) {
-  const R b0 = dq[0];
-  const R r1 = dq[1] - p.U * b0, r2 = dq[2] - p.V * b0, r3 = dq[3] - p.W * b0;
-  const R E = p.U * p.U + p.V * p.V + p.W * p.W + R(4) * kq * p.h2;  // |U|^2 + (K+3)/(2 lam)
-  const R r4 = R(2) * dq[4] - E * b0;
-  a[4] = p.lam * p.lam * kqi * (r4 - R(2) * (p.U * r1 + p.V * r2 + p.W * r3));  // 4 lam^2/(K+3)
-  const R tl = R(2) * p.lam;
-  a[1] = tl * r1 - p.U * a[4];
-  a[2] = tl * r2 - p.V * a[4];
-  a[3] = tl * r3 - p.W * a[4];
-  a[0] = b0 - p.U * a[1] - p.V * a[2] - p.W * a[3] - R(0.5) * a[4] * E;
 }
 
 // Euler state used for flux Jacobians in the local frame.
@@ -251,6 +222,94 @@ __device__ __forceinline__ void half_jet(const Prim<R>& p, R u0, R u1, R Eh, R K
   }
 }
 
+// Perturbation of the primitive variables, rho-weighted, for a perturbation
+// d of the conservative variables under the Maxwellian p:
+//   P = (d rho, rho dU, rho dV, rho dW, rho dlam).
+template <typename R>
+__device__ __forceinline__ void prim_pert(const Prim<R>& p, R kqi, const R d[5], R P[5]) {
+  P[0] = d[0];
+  P[1] = d[1] - p.U * d[0];
+  P[2] = d[2] - p.V * d[0];
+  P[3] = d[3] - p.W * d[0];
+  const R de = d[4] - p.U * d[1] - p.V * d[2] - p.W * d[3] + R(0.5) * (p.U * p.U + p.V * p.V + p.W * p.W) * d[0];
+  P[4] = p.lam * (d[0] - p.lam * kqi * de);
+}
+
+// Change of the normalised moment <u^n> (half line with boundary term Eh, or
+// full line with Eh = 0) under rho dU = PU, rho dlam = Pl, divided by rho:
+//   d<u^0> = Eh (2 lam dU + U dlam),  d<u^1> = <u^0> dU - Eh dlam/(2 lam),
+//   d<u^n> = n <u^{n-1}> dU - n (n-1) <u^{n-2}> dlam/(4 lam^2),  n >= 2.
+template <int n, typename R>
+__device__ __forceinline__ R dmom_u(const Mom<R>& M, const Prim<R>& p, R Eh, R PU, R Pl, R h22) {
+  if constexpr (n == 0) return Eh * (R(2) * p.lam * PU + p.U * Pl);
+  else if constexpr (n == 1) return M.u[0] * PU - p.h2 * Eh * Pl;
+  else return R(n) * M.u[n - 1] * PU - R(n * (n - 1)) * h22 * M.u[n - 2] * Pl;
+}
+// The same for a full-line Gaussian moment <v^n> (m = M.v or M.w, Pv = rho dV or rho dW).
+template <int n, typename R>
+__device__ __forceinline__ R dmom_g(const R* m, R Pv, R Pl, R h22) {
+  if constexpr (n == 0) return R(0);
+  else if constexpr (n == 1) return Pv;
+  else return R(n) * m[n - 1] * Pv - R(n * (n - 1)) * h22 * m[n - 2] * Pl;
+}
+
+// Derivative of Phi = rho <u^a v^b w^c psi> (moments M of one Maxwellian,
+// half-line boundary term Eh) along the perturbation P of prim_pert.
+//
+// With g_x = (a.psi) g (the micro-slope of Section 2.1), rho <phi (a.psi)>
+// over the same velocity range is exactly this derivative; it replaces the
+// moment sums of the micro-slope and time-slope terms of Eq. flux.
+template <int a, int b, int c, typename R>
+__device__ __forceinline__ void phi_jet(const Mom<R>& M, const Prim<R>& pm, R Eh, R Kint, const R P[5], R out[5]) {
+  const R h22 = pm.h2 * pm.h2;
+  // value and derivative of <u^i v^j w^k>
+  auto prod = [&](auto I, auto J, auto Kk, R& val, R& der) {
+    constexpr int i = decltype(I)::value, j = decltype(J)::value, k = decltype(Kk)::value;
+    const R ui = M.u[i], vj = M.v[j], wk = M.w[k];
+    const R dui = dmom_u<i>(M, pm, Eh, P[1], P[4], h22);
+    const R dvj = dmom_g<j>(M.v, P[2], P[4], h22);
+    const R dwk = dmom_g<k>(M.w, P[3], P[4], h22);
+    val = ui * vj * wk;
+    der = dui * vj * wk + ui * (dvj * wk + vj * dwk);
+  };
+  using std::integral_constant;
+  R v0, d0, v1, d1, v2, d2, v3, d3, va, da, vb, db, vc, dc;
+  prod(integral_constant<int, a>{}, integral_constant<int, b>{}, integral_constant<int, c>{}, v0, d0);
+  prod(integral_constant<int, a + 1>{}, integral_constant<int, b>{}, integral_constant<int, c>{}, v1, d1);
+  prod(integral_constant<int, a>{}, integral_constant<int, b + 1>{}, integral_constant<int, c>{}, v2, d2);
+  prod(integral_constant<int, a>{}, integral_constant<int, b>{}, integral_constant<int, c + 1>{}, v3, d3);
+  prod(integral_constant<int, a + 2>{}, integral_constant<int, b>{}, integral_constant<int, c>{}, va, da);
+  prod(integral_constant<int, a>{}, integral_constant<int, b + 2>{}, integral_constant<int, c>{}, vb, db);
+  prod(integral_constant<int, a>{}, integral_constant<int, b>{}, integral_constant<int, c + 2>{}, vc, dc);
+  const R X1 = Kint * pm.h2, dX1 = R(-2) * Kint * h22 * P[4];  // <xi^2> = K/(2 lam)
+  out[0] = P[0] * v0 + d0;
+  out[1] = P[0] * v1 + d1;
+  out[2] = P[0] * v2 + d2;
+  out[3] = P[0] * v3 + d3;
+  out[4] = R(0.5) * (P[0] * (va + vb + vc + v0 * X1) + da + db + dc + d0 * X1 + v0 * dX1);
+}
+
+// X = sum_j rho <u u_j psi a_j>, the spatial-slope term of the
+// non-equilibrium part of Eq. flux for one side (Maxwellian p with moments M
+// over its half line, slopes d[j] of the conservative variables along the
+// local axes j = n, t1, t2).  On the full line (Eh = 0) it is the
+// rho0 <u (abar.u) psi> term of the equilibrium part.
+template <typename R>
+__device__ __forceinline__ void side_terms(const Prim<R>& p, const Mom<R>& M, R Eh, R Kint, R kqi, const R d[3][5],
+                                           R X[5]) {
+  R P[5], t[5];
+  prim_pert(p, kqi, d[0], P);
+  phi_jet<2, 0, 0>(M, p, Eh, Kint, P, X);
+  prim_pert(p, kqi, d[1], P);
+  phi_jet<1, 1, 0>(M, p, Eh, Kint, P, t);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) X[i] += t[i];
+  prim_pert(p, kqi, d[2], P);
+  phi_jet<1, 0, 1>(M, p, Eh, Kint, P, t);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) X[i] += t[i];
+}
+
 template <typename R>
 struct FluxParams {
   R gamma, Kint, kq, kqi, mu_ref, T_ref, visc_exp, Pr, tau_c;  // kq = (K+3)/4, kqi = 1/kq
@@ -270,24 +329,6 @@ __device__ __forceinline__ FluxParams<R> flux_params(const DevParams& P) {
   return F;
 }
 
-// <u psi_i P> for P = a.u (a_j micro-slopes along x, y, z, rho-weighted),
-// expanded into the twelve monomials of P.
-template <typename R>
-__device__ __forceinline__ void flux_of_slope(const Mom<R>& M, const R a[3][5], R X[5]) {
-  // P = sum_j u_j (a_j0 + a_j1 u + a_j2 v + a_j3 w + a_j4 psi4)
-  const R pu = a[0][0], pv = a[1][0], pw = a[2][0];
-  const R puu = a[0][1], puv = a[0][2] + a[1][1], puw = a[0][3] + a[2][1];
-  const R pvv = a[1][2], pvw = a[1][3] + a[2][2], pww = a[2][3];
-  const R pu4 = a[0][4], pv4 = a[1][4], pw4 = a[2][4];
-  sfor<5>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    X[i] = pu * mpsi<i, 2, 0, 0, 0>(M) + pv * mpsi<i, 1, 1, 0, 0>(M) + pw * mpsi<i, 1, 0, 1, 0>(M) +
-           puu * mpsi<i, 3, 0, 0, 0>(M) + puv * mpsi<i, 2, 1, 0, 0>(M) + puw * mpsi<i, 2, 0, 1, 0>(M) +
-           pvv * mpsi<i, 1, 2, 0, 0>(M) + pvw * mpsi<i, 1, 1, 1, 0>(M) + pww * mpsi<i, 1, 0, 2, 0>(M) +
-           pu4 * mpsi2<i, 4, 2, 0, 0>(M) + pv4 * mpsi2<i, 4, 1, 1, 0>(M) + pw4 * mpsi2<i, 4, 1, 0, 1>(M);
-  });
-}
-
 // Gas-kinetic flux in the local frame (normal = first axis).
 //   ql, qr: conservative states on the two sides of the Gauss point
 //   dl[j], dr[j]: their derivatives along the local axes j = n, t1, t2
@@ -297,7 +338,7 @@ __device__ void gks_flux(const R ql[5], const R dl[3][5], const R qr[5], const R
                          const FluxParams<R>& P, R F[5], R dF[5]) {
   const R K = P.Kint;
   const Prim<R> pl = prim_of(ql, P.kq, P.kqi), pr = prim_of(qr, P.kq, P.kqi);
-  constexpr int NU = VISC ? 7 : 3;
+  constexpr int NU = VISC ? 5 : 3;
   Mom<R> Ml, Mr;
   R El, Er;
   moments<NU>(pl, +1, K, Ml, El);
@@ -343,60 +384,55 @@ __device__ void gks_flux(const R ql[5], const R dl[3][5], const R qr[5], const R
     const R plp = pl.rho * pl.h2, prp = pr.rho * pr.h2, p0p = p0.rho * p0.h2;
     // collision time: tau = mu(T0)/p0 + C dt |p_l - p_r|/(p_l + p_r), T = p/rho
     R mu = P.mu_ref;
-    if (P.visc_exp != R(0) && mu != R(0)) mu = P.mu_ref * pow(p0.h2 / P.T_ref, P.visc_exp);  // T0 = 1/(2 lam0)
+    // (T0/T_ref)^e as exp(e log(T0/T_ref)): a few units in the last place,
+    // for about half the cost of pow
+    if (P.visc_exp != R(0) && mu != R(0)) mu = P.mu_ref * exp(P.visc_exp * log(p0.h2 / P.T_ref));  // T0 = 1/(2 lam0)
     const R tau = mu / p0p + P.tau_c * dt * fabs(plp - prp) / (plp + prp);
     if (!(tau > R(0))) {
 #pragma unroll
       for (int i = 0; i < 5; ++i) { F[i] = Fe[i]; dF[i] = Ye[i]; }
       return;
     }
-    // rho0 abar_j and rho0 Abar
-    R ab[3][5];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) micro_slope_rho(p0, P.kq, P.kqi, dq0[j], ab[j]);
+    // rho0 <u (abar.u) psi> on the full line of g0
     Mom<R> M0;
     R E0;
-    moments<7>(p0, 0, K, M0, E0);
+    moments<5>(p0, 0, K, M0, E0);
     R X0[5];
-    flux_of_slope(M0, ab, X0);  // rho0 <u (abar.u) psi>
-    // side terms: rho_k A^k from <a^k.u + A^k> = 0, full-space moments of g_k
-    R Al[5], Ar[5], tmp[5], s1[5], s2[5];
+    side_terms(p0, M0, E0, K, P.kqi, dq0, X0);
+    // side terms of the initial non-equilibrium distribution
+    R Xl[5], Xr[5], Nk[5], Yk[5];
+    side_terms(pl, Ml, El, K, P.kqi, dl, Xl);
+    side_terms(pr, Mr, Er, K, P.kqi, dr, Xr);
     {
+      R tmp[5], s1[5], s2[5], Pp[5], yl[5], yr[5], nl[5], nr[5];
+      // rho_l <u A^l psi> over u > 0
       const EState<R> sl = estate(ql, P.gamma);
       euler_jv<0>(sl, dl[0], tmp);
       euler_jv<1>(sl, dl[1], s1);
       euler_jv<2>(sl, dl[2], s2);
 #pragma unroll
       for (int i = 0; i < 5; ++i) tmp[i] = -(tmp[i] + s1[i] + s2[i]);
-      micro_slope_rho(pl, P.kq, P.kqi, tmp, Al);
+      prim_pert(pl, P.kqi, tmp, Pp);
+      phi_jet<1, 0, 0>(Ml, pl, El, K, Pp, yl);
+      // rho_r <u A^r psi> over u < 0
       const EState<R> sr = estate(qr, P.gamma);
       euler_jv<0>(sr, dr[0], tmp);
       euler_jv<1>(sr, dr[1], s1);
       euler_jv<2>(sr, dr[2], s2);
 #pragma unroll
       for (int i = 0; i < 5; ++i) tmp[i] = -(tmp[i] + s1[i] + s2[i]);
-      micro_slope_rho(pr, P.kq, P.kqi, tmp, Ar);
-    }
-    R al[3][5], ar[3][5];  // rho_k a^k_j
+      prim_pert(pr, P.kqi, tmp, Pp);
+      phi_jet<1, 0, 0>(Mr, pr, Er, K, Pp, yr);
+      // rho <u psi>: the derivative along P = (1, 0, 0, 0, 0) is the value
+      const R e0[5] = {R(1), R(0), R(0), R(0), R(0)};
+      phi_jet<1, 0, 0>(Ml, pl, El, K, e0, nl);
+      phi_jet<1, 0, 0>(Mr, pr, Er, K, e0, nr);
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      micro_slope_rho(pl, P.kq, P.kqi, dl[j], al[j]);
-      micro_slope_rho(pr, P.kq, P.kqi, dr[j], ar[j]);
+      for (int i = 0; i < 5; ++i) {
+        Nk[i] = pl.rho * nl[i] + pr.rho * nr[i];
+        Yk[i] = yl[i] + yr[i];
+      }
     }
-    R Xl[5], Xr[5], Nk[5], Yk[5];
-    flux_of_slope(Ml, al, Xl);
-    flux_of_slope(Mr, ar, Xr);
-    sfor<5>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      Nk[i] = pl.rho * mpsi<i, 1, 0, 0, 0>(Ml) + pr.rho * mpsi<i, 1, 0, 0, 0>(Mr);
-      R yl = R(0), yr = R(0);
-      sfor<5>([&](auto J) {
-        constexpr int j = decltype(J)::value;
-        yl += Al[j] * mpsi2<i, j, 1, 0, 0>(Ml);
-        yr += Ar[j] * mpsi2<i, j, 1, 0, 0>(Mr);
-      });
-      Yk[i] = yl + yr;
-    });
     // time-integral coefficients of the fit F = (4 I(dt/2) - I(dt))/dt,
     // dF = 4 (I(dt) - 2 I(dt/2))/dt^2, with h = dt/2, r = tau/h and
     // em = 1 - exp(-h/tau)
@@ -616,10 +652,8 @@ __global__ void __launch_bounds__(kBlock) k_ghost(DevMesh m, DevParams P, double
     const double n[3] = {m.gnrm[g], m.gnrm[m.ng + g], m.gnrm[2 * m.ng + g]};
     farfield(q, P.qinf, n, P.gamma, o);
   }
-  for (int k = 0; k < 5; ++k) {
-    Q[k * m.nce + m.nc + g] = o[k];
-    if (Qf) Qf[k * m.nce + m.nc + g] = (float)o[k];
-  }
+  for (int k = 0; k < 5; ++k) Q[k * m.nce + m.nc + g] = o[k];
+  if (Qf) store_qf(Qf, m.nc + g, o);
 }
 
 // WENO reconstruction, one thread per cell.  Output coef[(v*10+j)*nc + c]:
@@ -774,11 +808,11 @@ __global__ void __launch_bounds__(kRThreads) k_recon(DevMesh m, DevParams P, con
   // this warp's variable: stencil differences (overlaps the staging)
   Real qv = Real(0);
   if (valid) {
-    qv = (Real)Q[v * m.nce + c];
+    qv = (Real)qget(Q, m.nce, v, c);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int64_t j = m.sten[(int64_t)k * nc + c];
-      sdq[(v * K + k) * kRC + lane] = (Real)Q[v * m.nce + j] - qv;
+      sdq[(v * K + k) * kRC + lane] = (Real)qget(Q, m.nce, v, j) - qv;
     }
   }
   if constexpr (STAGE) {
@@ -842,6 +876,117 @@ __global__ void __launch_bounds__(kRThreads) k_recon(DevMesh m, DevParams P, con
   const Real hi = cvt<Real>(m.hinv[c]);
   const Real glin = pick<Real>(P.glin, P.f_glin), g0 = Real(1) - Real(M) * glin, eps = pick<Real>(P.eps, P.f_eps);
   recon_finish<Real, M>(a, b, qv, mi, hi, glin, g0, eps, coef + (int64_t)v * 10 * nc + c, nc);
+}
+
+// WENO reconstruction in binary32 (mixed precision), one block per kRC = 32
+// cells with one warp per conservative variable, as k_recon, but with every
+// input of the block staged in shared memory by all 160 threads before any
+// arithmetic:
+//   - the stencil neighbours' states, one 32-byte record (all five
+//     variables) per neighbour;
+//   - the block's rows of the binary64 pseudo-inverses, rounded to binary32
+//     on the way in (cvt<float>, the rounding k_recon applies), so the tile
+//     takes half the shared memory of a binary64 tile and more blocks fit on
+//     an SM;
+//   - the sub-stencil positions, the cells' own states, second moments and
+//     1/h.
+// The copy loops issue their loads back to back (coalesced rows of 32 cells
+// for the per-cell arrays), so each thread keeps many loads in flight.  The
+// arithmetic and its order are those of k_recon.
+template <int K, int M, int KM>
+struct ReconSmemF {
+  static constexpr int kRows = 9 * K + M * 3 * KM;
+  static constexpr size_t tile = sizeof(float) * kRows * kRC;  // binary32 rows
+  static constexpr size_t nbr = sizeof(float) * 5 * K * kRC;   // neighbour states [5][K][kRC]
+  static constexpr size_t own = sizeof(float) * 5 * kRC;       // own states [5][kRC]
+  static constexpr size_t geo = sizeof(float) * 7 * kRC;       // mom (6) and 1/h [7][kRC]
+  static constexpr size_t sub = (size_t)M * KM * kRC;          // sub-stencil positions
+  static constexpr size_t bytes = tile + nbr + own + geo + sub;
+};
+
+template <int K, int M, int KM>
+__global__ void __launch_bounds__(kRThreads) k_recon_rs(DevMesh m, DevParams P, const float* __restrict__ Qf,
+                                                        float* __restrict__ coef, Control* __restrict__ ctl) {
+  using S = ReconSmemF<K, M, KM>;
+  constexpr int kRows = S::kRows;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float* tile = reinterpret_cast<float*>(smem_raw);                              // [kRows][kRC]
+  float* snbr = reinterpret_cast<float*>(smem_raw + S::tile);                    // [5][K][kRC]
+  float* sown = reinterpret_cast<float*>(smem_raw + S::tile + S::nbr);           // [5][kRC]
+  float* sgeo = reinterpret_cast<float*>(smem_raw + S::tile + S::nbr + S::own);  // [7][kRC]
+  uint8_t* ssub = smem_raw + S::tile + S::nbr + S::own + S::geo;                 // [M*KM][kRC]
+  if (m.nmesh == 1 && ctl->dt == 0.0) return;  // uniform over the grid (a batch computes every member)
+  const int64_t nc = m.nc, ncp = m.ncp;
+  const int t = threadIdx.x;
+  const int64_t c0 = (int64_t)blockIdx.x * kRC;
+  const int nv = nc - c0 < kRC ? (int)(nc - c0) : kRC;  // cells of this block
+  // neighbour and own states (records of 32 bytes)
+#pragma unroll 3
+  for (int e = t; e < (K + 1) * kRC; e += kRThreads) {
+    const int k = e >> 5, l = e & 31;
+    if (l < nv) {
+      const int64_t j = k < K ? (int64_t)__ldcs(m.sten + (int64_t)k * nc + c0 + l) : c0 + l;
+      const float4 a = __ldg(reinterpret_cast<const float4*>(Qf + 8 * j));
+      const float b = __ldg(Qf + 8 * j + 4);
+      float* dst = k < K ? snbr + k * kRC + l : sown + l;
+      const int vs = k < K ? K * kRC : kRC;  // stride between variables
+      dst[0] = a.x;
+      dst[vs] = a.y;
+      dst[2 * vs] = a.z;
+      dst[3 * vs] = a.w;
+      dst[4 * vs] = b;
+    }
+  }
+  // pseudo-inverse rows (pitch ncp: every row is readable for all 32 lanes)
+#pragma unroll 8
+  for (int e = t; e < kRows * kRC; e += kRThreads) {
+    const int r = e >> 5, l = e & 31;
+    const double* src = r < 9 * K ? m.pinv0 + (int64_t)r * ncp + c0 + l : m.pinvm + (int64_t)(r - 9 * K) * ncp + c0 + l;
+    tile[e] = cvt<float>(__ldcs(src));
+  }
+  for (int e = t; e < M * KM * kRC; e += kRThreads) ssub[e] = m.subidx[(int64_t)(e >> 5) * ncp + c0 + (e & 31)];
+  for (int e = t; e < 7 * kRC; e += kRThreads) {
+    const int r = e >> 5, l = e & 31;
+    if (l < nv) sgeo[e] = cvt<float>(r < 6 ? m.mom[(int64_t)r * nc + c0 + l] : m.hinv[c0 + l]);
+  }
+  __syncthreads();
+  const int lane = t & 31, v = t >> 5;
+  if (lane >= nv) return;
+  const int64_t c = c0 + lane;
+  const float qv = sown[v * kRC + lane];
+  float dq[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) dq[k] = snbr[(v * K + k) * kRC + lane] - qv;
+  auto row = [&](int r) -> float { return tile[r * kRC + lane]; };
+  // least-squares polynomials (the operation order of k_recon)
+  float a[9];
+#pragma unroll
+  for (int d = 0; d < 9; ++d) {
+    float sacc = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) sacc += row(d * K + k) * dq[k];
+    a[d] = sacc;
+  }
+  float b[M][3];
+#pragma unroll
+  for (int s = 0; s < M; ++s) {
+    float x[KM];
+#pragma unroll
+    for (int r = 0; r < KM; ++r) x[r] = snbr[(v * K + ssub[(s * KM + r) * kRC + lane]) * kRC + lane] - qv;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      float acc = 0.f;
+#pragma unroll
+      for (int r = 0; r < KM; ++r) acc += row(9 * K + (s * 3 + d) * KM + r) * x[r];
+      b[s][d] = acc;
+    }
+  }
+  float mi[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) mi[q] = sgeo[q * kRC + lane];
+  const float hi = sgeo[6 * kRC + lane];
+  const float glin = P.f_glin, g0 = 1.f - float(M) * glin, eps = P.f_eps;
+  recon_finish<float, M>(a, b, qv, mi, hi, glin, g0, eps, coef + (int64_t)v * 10 * nc + c, nc);
 }
 
 // Point value and gradient of the combined polynomial of cell c at offset d.
@@ -1050,14 +1195,15 @@ __global__ void __launch_bounds__(kBlock) k_update1(DevMesh m, const Real* __res
   if (dt == 0.0) return;
   double L[5], dL[5];
   gather<Real, NFC>(m, Fs, c, L, dL);
+  double qs[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     const double q = Q[v * m.nce + c];
-    const double qs = q + 0.5 * dt * L[v] + 0.125 * dt * dt * dL[v];
-    Qs[v * m.nce + c] = qs;
+    qs[v] = q + 0.5 * dt * L[v] + 0.125 * dt * dt * dL[v];
+    Qs[v * m.nce + c] = qs[v];
     R[v * m.nc + c] = q + dt * L[v] + dt * dt / 6.0 * dL[v];
-    if (Qf) Qf[v * m.nce + c] = (float)qs;
   }
+  if (Qf) store_qf(Qf, c, qs);
 }
 
 // Stage 2: Q^{n+1} = R + dt^2/3 dL(Q*); next step bound; non-finite flag.
@@ -1080,8 +1226,8 @@ __global__ void __launch_bounds__(kBlock) k_update2(DevMesh m, DevParams P, cons
       q[v] = R[v * m.nc + c] + dt * dt / 3.0 * dL[v];
       finite = finite && isfinite(q[v]);
       Q[v * m.nce + c] = q[v];
-      if (Qf) Qf[v * m.nce + c] = (float)q[v];
     }
+    if (Qf) store_qf(Qf, c, q);
     if (!finite) atomicOr(&ctl[mid].flags, FLAG_NONFINITE);
     bound = cell_dt(q, m.hdt[c], P);
     if (!(bound >= 0.0)) bound = __longlong_as_double(0x7ff0000000000000LL);
@@ -1090,9 +1236,13 @@ __global__ void __launch_bounds__(kBlock) k_update2(DevMesh m, DevParams P, cons
 }
 
 // Binary32 copy of the state (mixed precision).
-__global__ void k_tofloat(const double* __restrict__ Q, float* __restrict__ Qf, int64_t n) {
-  const int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x;
-  if (i < n) Qf[i] = (float)Q[i];
+__global__ void k_tofloat(const double* __restrict__ Q, float* __restrict__ Qf, int64_t nce) {
+  const int64_t c = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (c >= nce) return;
+  double q[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) q[v] = Q[v * nce + c];
+  store_qf(Qf, c, q);
 }
 
 __global__ void k_setdt(Control* ctl, int n, double dt) {
@@ -1112,18 +1262,35 @@ __global__ void k_operator(DevMesh m, const Real* __restrict__ Fs, double* __res
 
 inline unsigned blocks(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
+// Variants: binary64, 0 = rows staged by bulk asynchronous copies, 1 = rows
+// read directly; binary32, 0 = k_recon_rs, 1 = rows staged by bulk
+// asynchronous copies.
 template <typename Real, typename QT, int K, int M, int KM>
 void recon_launch(const DevMesh& m, const DevParams& p, const QT* Q, Real* coef, Control* ctl, cudaStream_t s,
                   bool prep) {
   using S = ReconSmem<Real, K, M, KM>;
-  if (prep) {
-    cudaFuncSetAttribute(k_recon<Real, QT, K, M, KM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
-    cudaFuncSetAttribute(k_recon<Real, QT, K, M, KM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::dq);
-    return;
-  }
   const unsigned nb = (unsigned)((m.nc + kRC - 1) / kRC);
-  if (p.recon_variant == 1) k_recon<Real, QT, K, M, KM, false><<<nb, kRThreads, S::dq, s>>>(m, p, Q, coef, ctl);
-  else k_recon<Real, QT, K, M, KM, true><<<nb, kRThreads, S::bytes, s>>>(m, p, Q, coef, ctl);
+  if constexpr (sizeof(Real) == 4) {
+    using SF = ReconSmemF<K, M, KM>;
+    if (prep) {
+      cudaFuncSetAttribute(k_recon<Real, QT, K, M, KM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)S::bytes);
+      cudaFuncSetAttribute(k_recon_rs<K, M, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SF::bytes);
+      return;
+    }
+    if (p.recon_variant == 1) k_recon<Real, QT, K, M, KM, true><<<nb, kRThreads, S::bytes, s>>>(m, p, Q, coef, ctl);
+    else k_recon_rs<K, M, KM><<<nb, kRThreads, SF::bytes, s>>>(m, p, Q, coef, ctl);
+  } else {
+    if (prep) {
+      cudaFuncSetAttribute(k_recon<Real, QT, K, M, KM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)S::bytes);
+      cudaFuncSetAttribute(k_recon<Real, QT, K, M, KM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)S::dq);
+      return;
+    }
+    if (p.recon_variant == 1) k_recon<Real, QT, K, M, KM, false><<<nb, kRThreads, S::dq, s>>>(m, p, Q, coef, ctl);
+    else k_recon<Real, QT, K, M, KM, true><<<nb, kRThreads, S::bytes, s>>>(m, p, Q, coef, ctl);
+  }
 }
 
 // Stencil shapes compiled in: tetrahedra with 12..16 members and 4 sub-stencils
@@ -1171,8 +1338,9 @@ template <typename Real, int G, bool VISC>
 void flux_launch(const DevMesh& m, const DevParams& p, const Real* coef, Real* Fs, const Control* ctl, cudaStream_t s) {
   if (p.flux_variant == 1) {
     constexpr int FB = kBlock / G;
-    // binary32: 4 blocks of 128 per SM (128 registers); binary64: 2
-    k_flux_gp<Real, G, VISC, sizeof(Real) == 4 ? 4 : 2>
+    // binary32: 4 blocks of 128 per SM (128 registers), 3 with viscosity
+    // (168 registers, few spills); binary64: 2
+    k_flux_gp<Real, G, VISC, sizeof(Real) == 4 ? (VISC ? 3 : 4) : 2>
         <<<(unsigned)((m.nf + FB - 1) / FB), kBlock, 0, s>>>(m, p, coef, Fs, ctl);
   } else {
     k_flux<Real, G, VISC><<<blocks(m.nf), kBlock, 0, s>>>(m, p, coef, Fs, ctl);
@@ -1259,7 +1427,7 @@ void launch_control(const DevMesh& m, const DevWork& w, double t_end, double dt_
 void launch_reset(const DevMesh& m, const DevParams& p, const DevWork& w, int precision, int only, double t,
                   cudaStream_t s) {
   k_reset<<<(m.nmesh + 127) / 128, 128, 0, s>>>(w.ctl, m.nmesh, only, t);
-  if (precision == 1) k_tofloat<<<blocks(5 * m.nce), kBlock, 0, s>>>(w.Q, w.Qf, 5 * m.nce);
+  if (precision == 1) k_tofloat<<<blocks(m.nce), kBlock, 0, s>>>(w.Q, w.Qf, m.nce);
   k_dt<<<blocks(m.nc), kBlock, 0, s>>>(m, p, w.Q, w.ctl);
 }
 

@@ -754,7 +754,7 @@ int64_t device_bytes(const HostMesh& m, int precision) {
   // state and work arrays
   b += al(8 * 5 * nce) * 2;                    // Q, Q* (with ghost slots)
   b += al(8 * 5 * nc);                         // R (partial S2O4 sum)
-  if (precision == HGKS_FP32_MIXED) b += al(4 * 5 * nce);  // binary32 copy of the stage state
+  if (precision == HGKS_FP32_MIXED) b += al(4 * 8 * nce);  // binary32 copy of the stage state, 32 B per cell
   b += al(rs * 50 * nc);                       // reconstruction coefficients
   b += al(rs * 10 * nf);                       // face flux and its time slope
   b += 4096;                                   // control block

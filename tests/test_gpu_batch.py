@@ -71,11 +71,15 @@ def test_batch_reports_a_nonfinite_member():
 
 
 def _same(a, b, precision):
-    """FP64: bitwise.  FP32-mixed: the compiler may schedule binary32 operations
-    differently under different register caps, so equal to binary32 rounding."""
-    if precision == H.HGKS_FP64:
-        return np.array_equal(a, b)
-    return np.all(np.abs(a - b) <= 1e-6 * np.abs(b).max(axis=0))
+    """The variants run the same operations in the same order, but the compiler
+    may contract a multiply and an add into one fused operation in one kernel
+    and not in the other: equal to a few units of the last place of the
+    precision (FP64: 1e-14, FP32-mixed: 1e-6) of the magnitude of the
+    quantity (density, momentum vector, energy)."""
+    tol = 1e-14 if precision == H.HGKS_FP64 else 1e-6
+    mag = np.abs(b).max(axis=0)
+    mag[1:4] = mag[1:4].max()
+    return np.all(np.abs(a - b) <= tol * mag)
 
 
 @pytest.mark.parametrize("precision", [H.HGKS_FP64, H.HGKS_FP32_MIXED])
