@@ -908,7 +908,6 @@ template <int K, int M, int KM>
 __global__ void __launch_bounds__(kRThreads) k_recon_rs(DevMesh m, DevParams P, const float* __restrict__ Qf,
                                                         float* __restrict__ coef, Control* __restrict__ ctl) {
   using S = ReconSmemF<K, M, KM>;
-  constexpr int kRows = S::kRows;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* tile = reinterpret_cast<float*>(smem_raw);                              // [kRows][kRC]
   float* snbr = reinterpret_cast<float*>(smem_raw + S::tile);                    // [5][K][kRC]
@@ -920,38 +919,82 @@ __global__ void __launch_bounds__(kRThreads) k_recon_rs(DevMesh m, DevParams P, 
   const int t = threadIdx.x;
   const int64_t c0 = (int64_t)blockIdx.x * kRC;
   const int nv = nc - c0 < kRC ? (int)(nc - c0) : kRC;  // cells of this block
-  // neighbour and own states (records of 32 bytes)
-#pragma unroll 3
-  for (int e = t; e < (K + 1) * kRC; e += kRThreads) {
-    const int k = e >> 5, l = e & 31;
-    if (l < nv) {
-      const int64_t j = k < K ? (int64_t)__ldcs(m.sten + (int64_t)k * nc + c0 + l) : c0 + l;
-      const float4 a = __ldg(reinterpret_cast<const float4*>(Qf + 8 * j));
-      const float b = __ldg(Qf + 8 * j + 4);
-      float* dst = k < K ? snbr + k * kRC + l : sown + l;
-      const int vs = k < K ? K * kRC : kRC;  // stride between variables
-      dst[0] = a.x;
-      dst[vs] = a.y;
-      dst[2 * vs] = a.z;
-      dst[3 * vs] = a.w;
-      dst[4 * vs] = b;
+  // With 5 warps of 32 lanes, thread (v, lane) stages column `lane` of the
+  // rows v, v + 5, v + 10, ... of every per-cell array, so its addresses
+  // advance by a fixed stride.
+  const int lane = t & 31, v = t >> 5;
+  const bool live = lane < nv;
+  // 1. stencil indices of this thread's neighbour entries (entry K: the cell itself)
+  constexpr int NE = (K + 1 + 4) / 5;
+  int32_t jn[NE];
+#pragma unroll
+  for (int i = 0; i < NE; ++i) {
+    const int k = v + 5 * i;
+    jn[i] = (k < K && live) ? __ldcs(m.sten + (int64_t)k * nc + c0 + lane) : (int32_t)(c0 + lane);
+  }
+  // 2. first batch of pseudo-inverse rows (binary64, read once: streaming loads)
+  constexpr int R0 = 9 * K, R1 = M * 3 * KM;  // rows of pinv0 and pinvm
+  constexpr int N0 = (R0 + 4) / 5, N1 = (R1 + 4) / 5;
+  constexpr int B = 8;
+  const double* p0 = m.pinv0 + (int64_t)v * ncp + c0 + lane;
+  const double* p1 = m.pinvm + (int64_t)v * ncp + c0 + lane;
+  const int64_t step = 5 * ncp;
+  double pv[B];
+#pragma unroll
+  for (int i = 0; i < B; ++i)
+    if (i < N0 && v + 5 * i < R0) pv[i] = __ldcs(p0 + i * step);
+  // 3. neighbour and own state records (32 bytes each)
+  float4 qa[NE];
+  float qb[NE];
+#pragma unroll
+  for (int i = 0; i < NE; ++i) {
+    if (v + 5 * i <= K && live) {
+      qa[i] = __ldg(reinterpret_cast<const float4*>(Qf + 8 * (int64_t)jn[i]));
+      qb[i] = __ldg(Qf + 8 * (int64_t)jn[i] + 4);
     }
   }
-  // pseudo-inverse rows (pitch ncp: every row is readable for all 32 lanes)
-#pragma unroll 8
-  for (int e = t; e < kRows * kRC; e += kRThreads) {
-    const int r = e >> 5, l = e & 31;
-    const double* src = r < 9 * K ? m.pinv0 + (int64_t)r * ncp + c0 + l : m.pinvm + (int64_t)(r - 9 * K) * ncp + c0 + l;
-    tile[e] = cvt<float>(__ldcs(src));
+  // 4. the first batch to binary32, then the remaining rows in batches
+#pragma unroll
+  for (int i = 0; i < B; ++i)
+    if (i < N0 && v + 5 * i < R0) tile[(v + 5 * i) * kRC + lane] = cvt<float>(pv[i]);
+#pragma unroll 1
+  for (int i0 = B; i0 < N0; i0 += B) {
+#pragma unroll
+    for (int i = 0; i < B; ++i)
+      if (i0 + i < N0 && v + 5 * (i0 + i) < R0) pv[i] = __ldcs(p0 + (i0 + i) * step);
+#pragma unroll
+    for (int i = 0; i < B; ++i)
+      if (i0 + i < N0 && v + 5 * (i0 + i) < R0) tile[(v + 5 * (i0 + i)) * kRC + lane] = cvt<float>(pv[i]);
   }
-  for (int e = t; e < M * KM * kRC; e += kRThreads) ssub[e] = m.subidx[(int64_t)(e >> 5) * ncp + c0 + (e & 31)];
-  for (int e = t; e < 7 * kRC; e += kRThreads) {
-    const int r = e >> 5, l = e & 31;
-    if (l < nv) sgeo[e] = cvt<float>(r < 6 ? m.mom[(int64_t)r * nc + c0 + l] : m.hinv[c0 + l]);
+#pragma unroll 1
+  for (int i0 = 0; i0 < N1; i0 += B) {
+#pragma unroll
+    for (int i = 0; i < B; ++i)
+      if (i0 + i < N1 && v + 5 * (i0 + i) < R1) pv[i] = __ldcs(p1 + (i0 + i) * step);
+#pragma unroll
+    for (int i = 0; i < B; ++i)
+      if (i0 + i < N1 && v + 5 * (i0 + i) < R1) tile[(R0 + v + 5 * (i0 + i)) * kRC + lane] = cvt<float>(pv[i]);
   }
+  // 5. neighbour states to shared memory ([5][K][kRC]; own states [5][kRC])
+#pragma unroll
+  for (int i = 0; i < NE; ++i) {
+    const int k = v + 5 * i;
+    if (k <= K && live) {
+      float* dst = k < K ? snbr + k * kRC + lane : sown + lane;
+      const int vs = k < K ? K * kRC : kRC;
+      dst[0] = qa[i].x;
+      dst[vs] = qa[i].y;
+      dst[2 * vs] = qa[i].z;
+      dst[3 * vs] = qa[i].w;
+      dst[4 * vs] = qb[i];
+    }
+  }
+  // 6. sub-stencil positions, second moments and 1/h
+  for (int r = v; r < M * KM; r += 5) ssub[r * kRC + lane] = m.subidx[(int64_t)r * ncp + c0 + lane];
+  for (int r = v; r < 7; r += 5)
+    if (live) sgeo[r * kRC + lane] = cvt<float>(r < 6 ? m.mom[(int64_t)r * nc + c0 + lane] : m.hinv[c0 + lane]);
   __syncthreads();
-  const int lane = t & 31, v = t >> 5;
-  if (lane >= nv) return;
+  if (!live) return;
   const int64_t c = c0 + lane;
   const float qv = sown[v * kRC + lane];
   float dq[K];
