@@ -6,7 +6,11 @@ step (time step, two stages of reconstruction, flux and update) of the whole
 mesh.  Metric: cell-updates/s = cells x steps / device time.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hgks|reference]
-                    [--precision fp64|mixed] [--workload density48|density24|sphere]
+                    [--precision fp64|mixed] [--workload densityN | densityNv | sphere | sphereN]
+                    [--no-cpu-baseline] [--no-serve] [--serve]
+
+densityN: N^3 x 6 tets (densityNv with mu = 1e-3, Pr = 0.72); sphere: the
+1.51M-cell hex shell at Ma 0.2535, Re 300; sphereN: a 6 x N^2 x 1.3N shell.
 
 Prints one JSON line (rank 0).  For N > 1 (torchrun) every rank advances its
 own replica of the workload: the path has no exchange step on one GPU per
@@ -28,12 +32,35 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# Executed binary64 operations per face of the flux kernel and per cell of
-# the reconstruction kernel (FP64 path), counted by ncu on the kernels as
-# built (sass dadd + dmul + 2 dfma per launch, divided by the faces or cells
-# of the launch); see profiles/flux_fp64_density12.md.  None until measured.
-FP64_FLOPS_PER_FACE_INVISCID = 6429  # ncu: 133.31 Mflop per launch / 20736 faces (12^3 x 6 mesh)
+# Executed binary64 operations per face of the FP64 flux kernel
+# k_flux_gp<double, 3, inviscid> (sass dadd + dmul + 2 dfma per launch,
+# divided by the faces of the launch, ncu on the 12^3 x 6 mesh), and its DRAM
+# bytes per face (dram__bytes_read + dram__bytes_write of one launch on the
+# 40^3 x 6 mesh, 768,000 faces, larger than L2; the traffic grows with the
+# faces).  Set to None when the kernel changes until measured again.
+FP64_FLOPS_PER_FACE_INVISCID = 5037  # 104.45 Mflop per launch / 20736 faces
+FP64_FLUX_DRAM_BYTES_PER_FACE = 497.07  # (330.75 + 51.01) MB / 768000 faces
+# Algorithmic bytes per cell of one binary32 reconstruction launch (k_recon_rs)
+# on tetrahedra: binary64 pseudo-inverse rows (9K + 3 M KM) x 8 B, sub-stencil
+# positions M KM, stencil indices 4K, second moments and 1/h 7 x 8 B, the
+# cell's own 32-byte state record, and the 50 binary32 coefficients written.
+# Neighbour records are gathered through L2 and not counted.
+def recon_rs_bytes_per_cell(K: int, M: int = 4, KM: int = 6) -> int:
+    return (9 * K + 3 * M * KM) * 8 + M * KM + 4 * K + 7 * 8 + 32 + 50 * 4
+
+
 FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12  # SMs x DFMA/clk x 2 flop x max SM clock
+
+
+def _hbm_peak():
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6400.0  # fallback figure
+
+
+HBM_PEAK_GBS = _hbm_peak()
 
 
 def workload(name: str):
@@ -108,7 +135,7 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def cpu_baseline(w, budget_steps: int = 1):
+def cpu_baseline(w, budget_steps: int = 3):
     """The CPU checker as it stands, all host cores, on one step of the same mesh."""
     import oracle
 
@@ -201,9 +228,17 @@ def mixed_vs_fp64(H, w, stream, K, W):
     linf = {name: float(np.abs(a[:, v] - b[:, v]).max() / np.abs(b[:, v]).max())
             for name, v in (("rho", 0), ("rhoU", 1), ("rhoE", 4))}
     s.close()
-    return {"value": nc * K / (ms * 1e-3), "unit": "cell-updates/s", "ms_per_step": ms / K, "dtype": "f32-mixed",
-            "kernel_ms_per_step": {"ghost+recon": prof[1], "flux": prof[2], "update": prof[3]},
-            "error_vs_fp64_after_20_steps": {"l1_rel": l1, "linf_rel": linf, "dt": dts[0]}}
+    res = {"value": nc * K / (ms * 1e-3), "unit": "cell-updates/s", "ms_per_step": ms / K, "dtype": "f32-mixed",
+           "kernel_ms_per_step": {"ghost+recon": prof[1], "flux": prof[2], "update": prof[3]},
+           "error_vs_fp64_after_20_steps": {"l1_rel": l1, "linf_rel": linf, "dt": dts[0]}}
+    if len(w["cells"][0]) == 4 and w["periods"] is not None:
+        kst = H.Mesh(w["xyz"], w["cells"], w["periods"]).stencil_size
+        per_launch = recon_rs_bytes_per_cell(kst) * nc
+        ach = per_launch / (prof[1] / 2 * 1e-3) / 1e9  # two reconstruction launches per step, no ghosts
+        res["roofline_recon"] = {"bound": "hbm", "kernel": "k_recon_rs (binary32)", "achieved": ach,
+                                 "peak": HBM_PEAK_GBS, "unit": "GB/s", "frac": ach / HBM_PEAK_GBS,
+                                 "bytes_per_launch": per_launch, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+    return res
 
 
 def serve_run(H, small: bool, capacity=None):
@@ -245,7 +280,7 @@ def serve_run(H, small: bool, capacity=None):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="hgks", choices=["hgks", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
@@ -327,14 +362,18 @@ def main():
     prof = solver.profile(K)
     flux_ms = prof[2] / 2.0  # two flux launches per step
     nf = H.Mesh(w["xyz"], w["cells"], w["periods"], w.get("bfn"), w.get("bft")).n_faces
-    roof = {"bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS, "kernel": "k_flux (FP64)",
+    roof = {"bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS, "kernel": "k_flux_gp (FP64)",
             "peak_source": "derived: 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz (measured FMA chain: 1.125 TFLOP/s)",
             "achieved": None, "frac": None, "traffic": None,
             "kernel_ms_per_step": {"finalize": prof[0], "ghost+recon": prof[1], "flux": prof[2], "update": prof[3]}}
-    if FP64_FLOPS_PER_FACE_INVISCID and prec == H.HGKS_FP64 and not w["params"]:
+    if FP64_FLOPS_PER_FACE_INVISCID and prec == H.HGKS_FP64 and not w["params"] and len(w["cells"][0]) == 4:
         ach = FP64_FLOPS_PER_FACE_INVISCID * nf / (flux_ms * 1e-3) / 1e12
         roof["achieved"] = ach
         roof["frac"] = ach / FP64_PEAK_TFLOPS
+        roof["flop_per_launch"] = FP64_FLOPS_PER_FACE_INVISCID * nf
+        if FP64_FLUX_DRAM_BYTES_PER_FACE:
+            roof["traffic"] = FP64_FLUX_DRAM_BYTES_PER_FACE * nf
+            roof["traffic_source"] = "ncu dram bytes per face of one launch on the 40^3 x 6 mesh, times the faces"
 
     # ---- end to end through the C ABI with host buffers: per step the state
     # goes host -> device, one step runs, the state comes back
