@@ -95,7 +95,7 @@ typedef struct {
  *                  units in the last place (the compiler may fuse a
  *                  multiply and an add in one variant and not in another);
  *                  each variant is deterministic.  0: the defaults, flux per
- *                  Gauss point, rows staged.
+ *                  face, rows staged.
  *   stream         cudaStream_t to run on, or NULL for a library stream. */
 typedef struct {
   double gamma, mu_ref, T_ref, visc_exp, Pr, cfl, tau_num_c, weno_eps, weno_gamma_lin;

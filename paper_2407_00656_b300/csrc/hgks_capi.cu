@@ -324,8 +324,9 @@ int create_solver(hgks_mesh* const* meshes, int n, const hgks_params* params, co
   w.R = cv.take<double>(5 * m.nc);
   w.Qf = s->precision == HGKS_FP32_MIXED ? cv.take<float>(8 * dm.nce) : nullptr;
   const int64_t rs = s->precision == HGKS_FP32_MIXED ? 4 : 8;
-  w.coef = cv.take<char>(rs * 50 * m.nc);
-  w.Fs = cv.take<char>(rs * 10 * m.nf);
+  const bool f32 = s->precision == HGKS_FP32_MIXED;
+  w.coef = cv.take<char>(rs * (f32 ? hgks::kCoefRec32 : hgks::kCoefRec64) * m.nc);
+  w.Fs = cv.take<char>(rs * (f32 ? hgks::kFluxRec32 : hgks::kFluxRec64) * m.nf);
   int32_t* p_cmesh = n > 1 ? cv.take<int32_t>(m.nc) : nullptr;
   hgks::Control* p_ctl = cv.take<hgks::Control>(n);
   w.ctl = p_ctl;
@@ -375,7 +376,7 @@ int create_solver(hgks_mesh* const* meshes, int n, const hgks_params* params, co
   for (int i = 0; i < 5; ++i) dp.qinf[i] = params->q_inf[i];
   dp.viscous = (params->mu_ref > 0.0 || params->tau_num_c > 0.0) ? 1 : 0;
   hgks::fill_float_params(dp);
-  dp.flux_variant = 1;
+  dp.flux_variant = 0;
   dp.recon_variant = 0;
   hgks::prepare_kernels(dm, s->precision);
   // initial states

@@ -69,6 +69,13 @@ inline void fill_float_params(DevParams& p) {
   for (int i = 0; i < 5; ++i) p.f_qinf[i] = (float)p.qinf[i];
 }
 
+// Reals per record of the reconstruction coefficients (one record per cell:
+// 5 variables x 10 coefficients) and of the face fluxes (one record per face:
+// F then dF/dt, 5 each).  Binary32 records are padded to a multiple of 16
+// bytes so that they can be moved with 16-byte vector accesses.
+constexpr int kCoefRec64 = 50, kCoefRec32 = 52;
+constexpr int kFluxRec64 = 10, kFluxRec32 = 12;
+
 // Step control block in device memory.
 struct Control {
   double t;          // time reached by the queued steps
@@ -90,8 +97,9 @@ struct DevWork {
   double* R;      // [5][nc]  Q^n + dt L^n + dt^2/6 dL^n
   float* Qf;      // [nce][8] binary32 copy of the stage state, one 32-byte record per cell
                   // (5 variables, 3 zero pads; mixed precision only)
-  void* coef;     // [50][nc] reconstruction polynomials (double or float)
-  void* Fs;       // [10][nf] face flux sums: F (5) then dF/dt (5) (double or float)
+  void* coef;     // [nc][kCoefRec] reconstruction polynomials (double or float):
+                  // record of cell c: [v][j], j = 0: q, 1-3: g, 4-9: k
+  void* Fs;       // [nf][kFluxRec] face flux sums: F (5) then dF/dt (5) (double or float)
   Control* ctl;   // [nmesh] one control block per member mesh
 };
 

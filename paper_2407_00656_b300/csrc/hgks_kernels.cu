@@ -68,6 +68,35 @@ __device__ __forceinline__ double qget(const double* __restrict__ Q, int64_t nce
 }
 __device__ __forceinline__ float qget(const float* __restrict__ Q, int64_t, int v, int64_t c) { return Q[8 * c + v]; }
 
+// Records of the reconstruction coefficients and face fluxes (see DevWork).
+template <typename Real>
+__host__ __device__ constexpr int coef_rec() { return sizeof(Real) == 4 ? kCoefRec32 : kCoefRec64; }
+template <typename Real>
+__host__ __device__ constexpr int flux_rec() { return sizeof(Real) == 4 ? kFluxRec32 : kFluxRec64; }
+
+// Ten consecutive reals at p (8-byte aligned for binary32, 16-byte for
+// binary64), as five vector accesses.
+__device__ __forceinline__ void load10(const float* __restrict__ p, float x[10]) {
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const float2 t = __ldg(reinterpret_cast<const float2*>(p) + i);
+    x[2 * i] = t.x;
+    x[2 * i + 1] = t.y;
+  }
+}
+__device__ __forceinline__ void load10(const double* __restrict__ p, double x[10]) {
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const double2 t = __ldg(reinterpret_cast<const double2*>(p) + i);
+    x[2 * i] = t.x;
+    x[2 * i + 1] = t.y;
+  }
+}
+__device__ __forceinline__ void store10(double* __restrict__ p, const double x[10]) {
+#pragma unroll
+  for (int i = 0; i < 5; ++i) reinterpret_cast<double2*>(p)[i] = make_double2(x[2 * i], x[2 * i + 1]);
+}
+
 // A parameter in the kernel's precision: the binary64 value or its copy
 // rounded to binary32 on the host.
 template <typename Real>
@@ -656,14 +685,15 @@ __global__ void __launch_bounds__(kBlock) k_ghost(DevMesh m, DevParams P, double
   if (Qf) store_qf(Qf, m.nc + g, o);
 }
 
-// WENO reconstruction, one thread per cell.  Output coef[(v*10+j)*nc + c]:
-// the combined polynomial P(x) = q + g.d + sum k_ab d_a d_b, d = x - centroid,
-// j = 0: q, 1-3: g, 4-9: k_xx k_yy k_zz k_xy k_yz k_zx.
+// The combined polynomial of a cell and variable is
+// P(x) = q + g.d + sum k_ab d_a d_b, d = x - centroid, stored as 10 reals
+// j = 0: q, 1-3: g, 4-9: k_xx k_yy k_zz k_xy k_yz k_zx at
+// coef[c * record + v * 10 + j].
 // Smoothness indicators, WENO-Z weights and the combined polynomial of one
-// variable (Section 2.3, Eq. weno), written to out[j*nc], j = 0..9.
+// variable (Section 2.3, Eq. weno), returned in out[j], j = 0..9.
 template <typename Real, int M>
 __device__ __forceinline__ void recon_finish(const Real a[9], const Real b[M][3], Real qv, const Real mi[6], Real hi,
-                                             Real glin, Real g0, Real eps, Real* __restrict__ out, int64_t nc) {
+                                             Real glin, Real g0, Real eps, Real out[10]) {
   // smoothness indicators (scaled coordinates; the |cell| powers cancel):
   // beta_0 = sum_a (a_a^2 + H_a.Mi.H_a) + sum_{|l|=2} (d^l P0)^2, beta_m = |b_m|^2
   const Real H[3][3] = {{Real(2) * a[3], a[6], a[8]}, {a[6], Real(2) * a[4], a[7]}, {a[8], a[7], Real(2) * a[5]}};
@@ -711,10 +741,10 @@ __device__ __forceinline__ void recon_finish(const Real a[9], const Real b[M][3]
   for (int q = 0; q < 6; ++q) q0 -= quad[q] * mi[q];
   out[0] = q0;
 #pragma unroll
-  for (int d = 0; d < 3; ++d) out[(1 + d) * nc] = lin[d] * hi;
+  for (int d = 0; d < 3; ++d) out[1 + d] = lin[d] * hi;
   const Real hi2 = hi * hi;
 #pragma unroll
-  for (int q = 0; q < 6; ++q) out[(4 + q) * nc] = quad[q] * hi2;
+  for (int q = 0; q < 6; ++q) out[4 + q] = quad[q] * hi2;
 }
 
 // --------------------------------------------------------------------------
@@ -755,16 +785,41 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return true;
 }
 
+constexpr int kRC = 32;
+constexpr int kRThreads = 5 * kRC;
+
+// Coefficient records of the block's cells (consecutive, so their records
+// are one contiguous run of memory): each (variable, cell) thread puts its
+// 10 reals into shared memory (pitch record + 1, which spreads a warp's
+// stores over the banks), then the block writes the run with coalesced
+// stores.  smem must hold kRC x (record + 1) reals and no longer be read by
+// any warp's arithmetic; every thread of the block calls this.
+template <typename Real>
+__device__ __forceinline__ void write_block_records(Real* smem, const Real res[10], bool live, int lane, int v,
+                                                    int nv, Real* __restrict__ coef, int64_t c0) {
+  constexpr int REC = coef_rec<Real>(), PITCH = REC + 1;
+  __syncthreads();
+  if (live) {
+#pragma unroll
+    for (int j = 0; j < 10; ++j) smem[lane * PITCH + v * 10 + j] = res[j];
+    if (v == 0)
+      for (int j = 50; j < REC; ++j) smem[lane * PITCH + j] = Real(0);
+  }
+  __syncthreads();
+  Real* dst = coef + c0 * REC;
+  for (int e = threadIdx.x; e < nv * REC; e += kRThreads) {
+    const int l = e / REC, r = e - l * REC;
+    dst[e] = smem[l * PITCH + r];
+  }
+}
+
 // WENO reconstruction, one block per kRC = 32 consecutive cells with one warp
 // per conservative variable (5 warps).  Warp 0 stages the block's rows of the
 // pseudo-inverses (9K quadratic rows, then 3*KM rows per sub-stencil; 32
 // cells of a row are 256 contiguous bytes) and the sub-stencil positions in
 // shared memory with bulk asynchronous copies, while every warp gathers its
 // variable's stencil differences; the rows are then reduced against them.
-// Output coef[(v*10+j)*nc + c]: P(x) = q + g.d + sum k_ab d_a d_b with
-// d = x - centroid; j = 0: q, 1-3: g, 4-9: k_xx k_yy k_zz k_xy k_yz k_zx.
-constexpr int kRC = 32;
-constexpr int kRThreads = 5 * kRC;
+// Output: the coefficient record of each cell (see recon_finish).
 
 template <typename Real, int K, int M, int KM>
 struct ReconSmem {
@@ -831,7 +886,8 @@ __global__ void __launch_bounds__(kRThreads) k_recon(DevMesh m, DevParams P, con
   } else {
     __syncwarp();
   }
-  if (!valid) return;
+  Real res[10];
+  if (valid) {
   auto row = [&](int r) -> Real {
     if constexpr (!STAGE)
       return cvt<Real>(r < 9 * K ? m.pinv0[(int64_t)r * ncp + c] : m.pinvm[(int64_t)(r - 9 * K) * ncp + c]);
@@ -875,7 +931,10 @@ __global__ void __launch_bounds__(kRThreads) k_recon(DevMesh m, DevParams P, con
   for (int q = 0; q < 6; ++q) mi[q] = cvt<Real>(m.mom[q * nc + c]);
   const Real hi = cvt<Real>(m.hinv[c]);
   const Real glin = pick<Real>(P.glin, P.f_glin), g0 = Real(1) - Real(M) * glin, eps = pick<Real>(P.eps, P.f_eps);
-  recon_finish<Real, M>(a, b, qv, mi, hi, glin, g0, eps, coef + (int64_t)v * 10 * nc + c, nc);
+  recon_finish<Real, M>(a, b, qv, mi, hi, glin, g0, eps, res);
+  }
+  const int nv = nc - c0 < kRC ? (int)(nc - c0) : kRC;
+  write_block_records<Real>(reinterpret_cast<Real*>(smem_raw), res, valid, lane, v, nv, coef, c0);
 }
 
 // WENO reconstruction in binary32 (mixed precision), one block per kRC = 32
@@ -994,8 +1053,8 @@ __global__ void __launch_bounds__(kRThreads) k_recon_rs(DevMesh m, DevParams P, 
   for (int r = v; r < 7; r += 5)
     if (live) sgeo[r * kRC + lane] = cvt<float>(r < 6 ? m.mom[(int64_t)r * nc + c0 + lane] : m.hinv[c0 + lane]);
   __syncthreads();
-  if (!live) return;
-  const int64_t c = c0 + lane;
+  float res[10];
+  if (live) {
   const float qv = sown[v * kRC + lane];
   float dq[K];
 #pragma unroll
@@ -1029,26 +1088,51 @@ __global__ void __launch_bounds__(kRThreads) k_recon_rs(DevMesh m, DevParams P, 
   for (int q = 0; q < 6; ++q) mi[q] = sgeo[q * kRC + lane];
   const float hi = sgeo[6 * kRC + lane];
   const float glin = P.f_glin, g0 = 1.f - float(M) * glin, eps = P.f_eps;
-  recon_finish<float, M>(a, b, qv, mi, hi, glin, g0, eps, coef + (int64_t)v * 10 * nc + c, nc);
+  recon_finish<float, M>(a, b, qv, mi, hi, glin, g0, eps, res);
+  }
+  write_block_records<float>(tile, res, live, lane, v, nv, coef, c0);
 }
 
 // Point value and gradient of the combined polynomial of cell c at offset d.
 template <typename Real>
-__device__ __forceinline__ void eval_poly(const Real* __restrict__ coef, int64_t nc, int64_t c, const Real d[3],
-                                          Real val[5], Real grad[5][3]) {
+__device__ __forceinline__ void eval_poly(const Real* __restrict__ coef, int64_t c, const Real d[3], Real val[5],
+                                          Real grad[5][3]) {
   const Real dxx = d[0] * d[0], dyy = d[1] * d[1], dzz = d[2] * d[2];
   const Real dxy = d[0] * d[1], dyz = d[1] * d[2], dzx = d[2] * d[0];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    const Real* p = coef + (int64_t)v * 10 * nc + c;
-    const Real q = p[0], gx = p[nc], gy = p[2 * nc], gz = p[3 * nc];
-    const Real kxx = p[4 * nc], kyy = p[5 * nc], kzz = p[6 * nc], kxy = p[7 * nc], kyz = p[8 * nc], kzx = p[9 * nc];
+    Real p[10];
+    load10(coef + c * coef_rec<Real>() + v * 10, p);
+    const Real q = p[0], gx = p[1], gy = p[2], gz = p[3];
+    const Real kxx = p[4], kyy = p[5], kzz = p[6], kxy = p[7], kyz = p[8], kzx = p[9];
     val[v] = q + gx * d[0] + gy * d[1] + gz * d[2] + kxx * dxx + kyy * dyy + kzz * dzz + kxy * dxy + kyz * dyz +
              kzx * dzx;
     grad[v][0] = gx + Real(2) * kxx * d[0] + kxy * d[1] + kzx * d[2];
     grad[v][1] = gy + Real(2) * kyy * d[1] + kxy * d[0] + kyz * d[2];
     grad[v][2] = gz + Real(2) * kzz * d[2] + kyz * d[1] + kzx * d[0];
   }
+}
+
+// Face flux record of face f: F (5) then dF/dt (5), binary32 records padded
+// to 12 reals.
+__device__ __forceinline__ void store_flux(float* __restrict__ Fs, int64_t f, const float x[10]) {
+  float4* r = reinterpret_cast<float4*>(Fs + f * kFluxRec32);
+  r[0] = make_float4(x[0], x[1], x[2], x[3]);
+  r[1] = make_float4(x[4], x[5], x[6], x[7]);
+  r[2] = make_float4(x[8], x[9], 0.f, 0.f);
+}
+__device__ __forceinline__ void store_flux(double* __restrict__ Fs, int64_t f, const double x[10]) {
+  store10(Fs + f * kFluxRec64, x);
+}
+__device__ __forceinline__ void load_flux(const float* __restrict__ Fs, int64_t f, float x[10]) {
+  const float4* r = reinterpret_cast<const float4*>(Fs + f * kFluxRec32);
+  const float4 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2);
+  x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+  x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+  x[8] = c.x; x[9] = c.y;
+}
+__device__ __forceinline__ void load_flux(const double* __restrict__ Fs, int64_t f, double x[10]) {
+  load10(Fs + f * kFluxRec64, x);
 }
 
 // Flux of Gauss point g of face f (Eq. flux at one point of the face
@@ -1059,7 +1143,7 @@ template <typename Real, int G, bool VISC>
 __device__ __forceinline__ Real point_flux(const DevMesh& m, const DevParams& P, const FluxParams<Real>& FP,
                                            const Real* __restrict__ coef, int64_t f, int g, int64_t own, int nbr,
                                            Real dt, Real r[10]) {
-  const int64_t nf = m.nf, nc = m.nc;
+  const int64_t nf = m.nf;
   // planar triangles share one normal; bilinear quads have one per point
   Real n[3], t1[3], t2[3];
   const int gn = G == 3 ? 0 : g;
@@ -1071,7 +1155,7 @@ __device__ __forceinline__ Real point_flux(const DevMesh& m, const DevParams& P,
   for (int a = 0; a < 3; ++a) d[a] = cvt<Real>(m.fdl[(g * 3 + a) * nf + f]);
   const Real wgt = cvt<Real>(m.fw[g * nf + f]);
   Real qv[5], gr[5][3];
-  eval_poly(coef, nc, own, d, qv, gr);
+  eval_poly(coef, own, d, qv, gr);
   // local frame: rotate momentum, take derivatives along n, t1, t2
   Real ql[5], dl[3][5], qr[5], dr[3][5];
   auto rot = [&](const Real x[5], Real y[5]) {
@@ -1098,7 +1182,7 @@ __device__ __forceinline__ Real point_flux(const DevMesh& m, const DevParams& P,
   if (nbr >= 0) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) d[a] = cvt<Real>(m.fdr[(g * 3 + a) * nf + f]);
-    eval_poly(coef, nc, (int64_t)nbr, d, qv, gr);
+    eval_poly(coef, (int64_t)nbr, d, qv, gr);
     local(qv, gr, qr, dr);
   } else if (nbr == -3) {
     // no-slip adiabatic wall: mirror state, momentum reversed, normal
@@ -1140,7 +1224,7 @@ __device__ __forceinline__ Real point_flux(const DevMesh& m, const DevParams& P,
 }
 
 // Face flux, one thread per face: sum over the Gauss points of weight*area
-// times the point flux.  Output Fs[j*nf + f], j = 0..4 F, 5..9 dF.
+// times the point flux.  Output: the flux record of each face (store_flux).
 template <typename Real, int G, bool VISC>
 __global__ void __launch_bounds__(kBlock) k_flux(DevMesh m, DevParams P, const Real* __restrict__ coef,
                                                  Real* __restrict__ Fs, const Control* __restrict__ ctl) {
@@ -1163,8 +1247,7 @@ __global__ void __launch_bounds__(kBlock) k_flux(DevMesh m, DevParams P, const R
 #pragma unroll
     for (int v = 0; v < 10; ++v) acc[v] = fma(w, r[v], acc[v]);
   }
-#pragma unroll
-  for (int v = 0; v < 10; ++v) Fs[v * nf + f] = acc[v];
+  store_flux(Fs, f, acc);
 }
 
 // Face flux, one thread per Gauss point: the G points of a face run on G
@@ -1194,14 +1277,17 @@ __global__ void __launch_bounds__(kBlock, MINB) k_flux_gp(DevMesh m, DevParams P
     for (int v = 0; v < 10; ++v) sr[gp][v][fl] = r[v];
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < 10 * FB; e += kBlock) {
-    const int v = e / FB, l = e - v * FB;
-    const int64_t ff = f0 + l;
-    if (ff >= nf) continue;
+  // the block's faces are consecutive records: write them as one contiguous run
+  constexpr int REC = flux_rec<Real>();
+  for (int e = threadIdx.x; e < REC * FB; e += kBlock) {
+    const int l = e / REC, v = e - l * REC;
+    if (f0 + l >= nf) break;
     Real acc = Real(0);
+    if (v < 10) {
 #pragma unroll
-    for (int g = 0; g < G; ++g) acc = fma(sw[g][l], sr[g][v][l], acc);
-    Fs[v * nf + ff] = acc;
+      for (int g = 0; g < G; ++g) acc = fma(sw[g][l], sr[g][v][l], acc);
+    }
+    Fs[f0 * REC + e] = acc;
   }
 }
 
@@ -1215,11 +1301,12 @@ __device__ __forceinline__ void gather(const DevMesh& m, const Real* __restrict_
   for (int p = 0; p < NFC; ++p) {
     const int32_t e = m.cface[p * m.nc + c];
     const int64_t f = e >> 1;
+    Real x[10];
+    load_flux(Fs, f, x);
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      const Real x = Fs[v * m.nf + f], y = Fs[(5 + v) * m.nf + f];
-      a[v] += (e & 1) ? -x : x;
-      b[v] += (e & 1) ? -y : y;
+      a[v] += (e & 1) ? -x[v] : x[v];
+      b[v] += (e & 1) ? -x[5 + v] : x[5 + v];
     }
   }
   const double vi = -m.volinv[c];

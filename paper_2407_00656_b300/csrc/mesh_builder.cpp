@@ -16,6 +16,8 @@
 //     bilinear quads, with per-point unit normals and weights times area.
 #include "mesh_builder.h"
 
+#include "hgks_internal.h"
+
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -755,8 +757,9 @@ int64_t device_bytes(const HostMesh& m, int precision) {
   b += al(8 * 5 * nce) * 2;                    // Q, Q* (with ghost slots)
   b += al(8 * 5 * nc);                         // R (partial S2O4 sum)
   if (precision == HGKS_FP32_MIXED) b += al(4 * 8 * nce);  // binary32 copy of the stage state, 32 B per cell
-  b += al(rs * 50 * nc);                       // reconstruction coefficients
-  b += al(rs * 10 * nf);                       // face flux and its time slope
+  const bool f32 = precision == HGKS_FP32_MIXED;
+  b += al(rs * (f32 ? kCoefRec32 : kCoefRec64) * nc);  // reconstruction coefficients
+  b += al(rs * (f32 ? kFluxRec32 : kFluxRec64) * nf);  // face flux and its time slope
   b += 4096;                                   // control block
   return b;
 }
