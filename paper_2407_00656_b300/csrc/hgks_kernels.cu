@@ -55,12 +55,30 @@ __device__ __forceinline__ float cvt<float>(double x) {
   return __uint_as_float(e < 897u ? sign : r);
 }
 
+// cvt<float> extended to the whole binary64 range: magnitudes of 2^128 and
+// above become a signed infinity, NaNs a quiet NaN (for state values, which
+// may be non-finite after a failed step).
+__device__ __forceinline__ float cvt_state(double x) {
+  const unsigned hi = (unsigned)((unsigned long long)__double_as_longlong(x) >> 32);
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  if (e < 1151u) return cvt<float>(x);
+  const bool nan = e == 0x7ffu && ((hi & 0xfffffu) | (unsigned)__double_as_longlong(x)) != 0u;
+  return __uint_as_float((hi & 0x80000000u) | 0x7f800000u | (nan ? 0x400000u : 0u));
+}
+
 // The binary32 state copy holds one 32-byte record per cell (5 variables and
 // 3 zero pads), so one stencil gather fetches all five variables of a cell.
-__device__ __forceinline__ void store_qf(float* __restrict__ Qf, int64_t c, const double q[5]) {
+// The rounded values are also returned in qf.
+__device__ __forceinline__ void store_qf(float* __restrict__ Qf, int64_t c, const double q[5], float qf[5]) {
+#pragma unroll
+  for (int v = 0; v < 5; ++v) qf[v] = cvt_state(q[v]);
   float4* r = reinterpret_cast<float4*>(Qf + 8 * c);
-  r[0] = make_float4((float)q[0], (float)q[1], (float)q[2], (float)q[3]);
-  r[1] = make_float4((float)q[4], 0.f, 0.f, 0.f);
+  r[0] = make_float4(qf[0], qf[1], qf[2], qf[3]);
+  r[1] = make_float4(qf[4], 0.f, 0.f, 0.f);
+}
+__device__ __forceinline__ void store_qf(float* __restrict__ Qf, int64_t c, const double q[5]) {
+  float qf[5];
+  store_qf(Qf, c, q, qf);
 }
 // Variable v of cell c of a state: binary64 [5][nce] or binary32 [nce][8].
 __device__ __forceinline__ double qget(const double* __restrict__ Q, int64_t nce, int v, int64_t c) {
@@ -95,6 +113,18 @@ __device__ __forceinline__ void load10(const double* __restrict__ p, double x[10
 __device__ __forceinline__ void store10(double* __restrict__ p, const double x[10]) {
 #pragma unroll
   for (int i = 0; i < 5; ++i) reinterpret_cast<double2*>(p)[i] = make_double2(x[2 * i], x[2 * i + 1]);
+}
+
+// binary32 -> binary64, exact.  Normal numbers and zeros are converted with
+// integer operations on the IEEE-754 fields (off the FP64 pipe); subnormals,
+// infinities and NaNs take the hardware conversion.
+__device__ __forceinline__ double f2d(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned e = (b >> 23) & 0xffu;
+  if ((b << 1) == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
+  if (e == 0u || e == 0xffu) return (double)x;
+  const unsigned hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)((b & 7u) << 29));
 }
 
 // A parameter in the kernel's precision: the binary64 value or its copy
@@ -616,6 +646,22 @@ __device__ __forceinline__ double cell_dt(const double q[5], double hdt, const D
   return dt;
 }
 
+// The same bound in binary32 from the binary32 state copy (mixed precision).
+__device__ __forceinline__ float cell_dt_f(const float q[5], float hdt, const DevParams& P) {
+  const float ri = 1.f / q[0];
+  const float u = q[1] * ri, v = q[2] * ri, w = q[3] * ri;
+  const float u2 = u * u + v * v + w * w;
+  const float p = (P.f_gamma - 1.f) * (q[4] - 0.5f * q[0] * u2);
+  const float a = sqrtf(P.f_gamma * p * ri);
+  float dt = hdt / (sqrtf(u2) + a);
+  if (P.mu_ref > 0.0) {
+    float mu = P.f_mu_ref;
+    if (P.visc_exp != 0.0) mu = P.f_mu_ref * powf(p * ri / P.f_T_ref, P.f_visc_exp);
+    dt = fminf(dt, q[0] * hdt * hdt / (2.f * mu));
+  }
+  return dt;
+}
+
 __device__ __forceinline__ void block_min_to(unsigned long long* dst, double v) {
   __shared__ double red[kBlock / 32];
   for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -652,15 +698,24 @@ __device__ __forceinline__ void member_min_to(const DevMesh& m, Control* ctl, in
 
 __device__ __forceinline__ int member_of(const DevMesh& m, int64_t c) { return m.cmesh ? m.cmesh[c] : 0; }
 
-__global__ void __launch_bounds__(kBlock) k_dt(DevMesh m, DevParams P, const double* __restrict__ Q, Control* ctl) {
+// Step bound of the state: binary64 from Q, or, in mixed precision (Qf
+// non-null), binary32 from the binary32 copy, as k_update2 computes it.
+__global__ void __launch_bounds__(kBlock) k_dt(DevMesh m, DevParams P, const double* __restrict__ Q,
+                                               const float* __restrict__ Qf, Control* ctl) {
   const int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x;
   double v = __longlong_as_double(0x7ff0000000000000LL);
   int mid = -1;
   if (i < m.nc) {
     mid = member_of(m, i);
-    double q[5];
-    for (int k = 0; k < 5; ++k) q[k] = Q[k * m.nce + i];
-    v = cell_dt(q, m.hdt[i], P);
+    if (Qf) {
+      float q[5];
+      for (int k = 0; k < 5; ++k) q[k] = Qf[8 * i + k];
+      v = f2d(cell_dt_f(q, cvt<float>(m.hdt[i]), P));
+    } else {
+      double q[5];
+      for (int k = 0; k < 5; ++k) q[k] = Q[k * m.nce + i];
+      v = cell_dt(q, m.hdt[i], P);
+    }
     if (!(v >= 0.0)) v = __longlong_as_double(0x7ff0000000000000LL);
   }
   member_min_to(m, ctl, mid, v);
@@ -1311,7 +1366,15 @@ __device__ __forceinline__ void gather(const DevMesh& m, const Real* __restrict_
   }
   const double vi = -m.volinv[c];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) { L[v] = (double)a[v] * vi; dL[v] = (double)b[v] * vi; }
+  for (int v = 0; v < 5; ++v) {
+    if constexpr (sizeof(Real) == 4) {
+      L[v] = f2d(a[v]) * vi;
+      dL[v] = f2d(b[v]) * vi;
+    } else {
+      L[v] = a[v] * vi;
+      dL[v] = b[v] * vi;
+    }
+  }
 }
 
 // Stage 1: Q* = Q + dt/2 L + dt^2/8 dL;  R = Q + dt L + dt^2/6 dL.
@@ -1357,9 +1420,14 @@ __global__ void __launch_bounds__(kBlock) k_update2(DevMesh m, DevParams P, cons
       finite = finite && isfinite(q[v]);
       Q[v * m.nce + c] = q[v];
     }
-    if (Qf) store_qf(Qf, c, q);
     if (!finite) atomicOr(&ctl[mid].flags, FLAG_NONFINITE);
-    bound = cell_dt(q, m.hdt[c], P);
+    if (Qf) {
+      float qf[5];
+      store_qf(Qf, c, q, qf);
+      bound = f2d(cell_dt_f(qf, cvt<float>(m.hdt[c]), P));
+    } else {
+      bound = cell_dt(q, m.hdt[c], P);
+    }
     if (!(bound >= 0.0)) bound = __longlong_as_double(0x7ff0000000000000LL);
   }
   member_min_to(m, ctl, dt != 0.0 ? mid : -1, bound);
@@ -1558,7 +1626,7 @@ void launch_reset(const DevMesh& m, const DevParams& p, const DevWork& w, int pr
                   cudaStream_t s) {
   k_reset<<<(m.nmesh + 127) / 128, 128, 0, s>>>(w.ctl, m.nmesh, only, t);
   if (precision == 1) k_tofloat<<<blocks(m.nce), kBlock, 0, s>>>(w.Q, w.Qf, m.nce);
-  k_dt<<<blocks(m.nc), kBlock, 0, s>>>(m, p, w.Q, w.ctl);
+  k_dt<<<blocks(m.nc), kBlock, 0, s>>>(m, p, w.Q, precision == 1 ? w.Qf : nullptr, w.ctl);
 }
 
 void launch_step(const DevMesh& m, const DevParams& p, const DevWork& w, int precision, cudaStream_t s,
