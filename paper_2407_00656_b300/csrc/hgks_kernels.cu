@@ -769,17 +769,41 @@ __device__ __forceinline__ void recon_finish(const Real a[9], const Real b[M][3]
     tz += fabs(beta0 - beta[s]);
   }
   tz *= Real(1) / Real(M);
-  // WENO-Z type weights
-  Real w0 = g0 * (Real(1) + tz / (beta0 + eps));
+  // WENO-Z type weights w_s = gamma_s (1 + tz / (beta_s + eps))
+  Real r[M + 1];  // r_s = tz / (beta_s + eps), s = 0: the big stencil
+  if constexpr (sizeof(Real) == 8) {
+    // binary64: the M + 1 reciprocals from one division, 1/x_i =
+    // (prod_{j<i} x_j)(prod_{j>i} x_j) / prod_j x_j (the binary64 pipe is the
+    // bound of this kernel; a division costs about ten of its operations)
+    Real x[M + 1], pre[M + 1];
+    x[0] = beta0 + eps;
+#pragma unroll
+    for (int s = 0; s < M; ++s) x[s + 1] = beta[s] + eps;
+    pre[0] = Real(1);
+#pragma unroll
+    for (int i = 1; i <= M; ++i) pre[i] = pre[i - 1] * x[i - 1];
+    const Real tinv = tz / (pre[M] * x[M]);
+    Real suf = Real(1);
+#pragma unroll
+    for (int i = M; i >= 0; --i) {
+      r[i] = pre[i] * suf * tinv;
+      suf *= x[i];
+    }
+  } else {
+    r[0] = tz / (beta0 + eps);
+#pragma unroll
+    for (int s = 0; s < M; ++s) r[s + 1] = tz / (beta[s] + eps);
+  }
+  const Real w0 = g0 * (Real(1) + r[0]);
   Real w[M];
   Real wsum = w0;
 #pragma unroll
   for (int s = 0; s < M; ++s) {
-    w[s] = glin * (Real(1) + tz / (beta[s] + eps));
+    w[s] = glin * (Real(1) + r[s + 1]);
     wsum += w[s];
   }
   const Real winv = Real(1) / wsum;
-  const Real c0 = w0 * winv / g0;  // wbar_0 / gamma_0
+  const Real c0 = (Real(1) + r[0]) * winv;  // wbar_0 / gamma_0
   Real lin[3] = {c0 * a[0], c0 * a[1], c0 * a[2]};
 #pragma unroll
   for (int s = 0; s < M; ++s) {
