@@ -258,7 +258,7 @@ def serve_run(H, small: bool, capacity=None):
     cache.warm(S.c5_requests(n=n, lo=lo, hi=hi, steps=steps, rate=1.0, seed=0, classes=classes))
     warm_s = time.perf_counter() - t0
     free, total = torch.cuda.mem_get_info()
-    budget = int(0.8 * free)
+    budget = int(0.7 * free)
     # capacity of this request mix: every request present at t = 0 (closed loop)
     burst = S.c5_requests(n=n, lo=lo, hi=hi, steps=steps, rate=1e9, seed=0, classes=classes)
     S.Server(mem_budget=budget, precision=H.HGKS_FP32_MIXED, chunk_steps=10, cache=cache).run(burst, time_limit=1800)

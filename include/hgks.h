@@ -32,6 +32,7 @@ extern "C" {
 
 typedef struct hgks_mesh hgks_mesh;     /* host-side mesh, built by hgks_mesh_create */
 typedef struct hgks_solver hgks_solver; /* device-resident solver state */
+typedef struct hgks_dmesh hgks_dmesh;   /* device-resident mesh, shared by solvers */
 
 enum {
   HGKS_OK = 0,
@@ -134,14 +135,41 @@ int hgks_mesh_clone(const hgks_mesh* mesh, hgks_mesh** out);
 
 /* Mesh facts: what = 0 cells, 1 faces, 2 boundary ghosts, 3 padded big
  * stencil size, 4 sub-stencil count, 5 device bytes hgks_init would allocate
- * for precision 0, 6 the same for precision 1.  Returns -1 for bad input. */
+ * for precision 0, 6 the same for precision 1, 7 of these the bytes of the
+ * static mesh arrays (a device mesh, hgks_dmesh_create), 8 and 9 the bytes of
+ * one solver's own state and work arrays for precision 0 and 1.  Returns -1
+ * for bad input. */
 int64_t hgks_mesh_info(const hgks_mesh* mesh, int what);
 
 /* Create a solver: copy the mesh and the initial cell averages q0
  * ([n_cells][5] host, caller order) to the device.  On HGKS_OK the solver owns
  * the mesh (do not destroy it separately); on failure the caller still owns
- * it.  Device memory is one cudaMalloc arena sized by hgks_mesh_info(.,5|6). */
+ * it.  Device memory: a device mesh (hgks_mesh_info(., 7) bytes) and the
+ * solver's arrays (8 | 9), both from the device's stream-ordered memory pool
+ * on the solver's stream.  The library raises the pool's release threshold,
+ * so freed blocks stay with the process for reuse (cudaMemPoolTrimTo returns
+ * them). */
 int hgks_init(hgks_mesh* mesh, const hgks_params* params, const double* q0, hgks_solver** out);
+
+/* Device mesh: the static arrays of a built mesh (geometry, connectivity,
+ * stencils, pseudo-inverses, face quadrature) in device memory, immutable and
+ * shared by any number of solvers (no counterpart in the paper: the serving
+ * loop keeps one per geometry resident).  hgks_dmesh_create copies; the host
+ * mesh stays with the caller.  stream: the cudaStream_t to copy on (NULL: a
+ * library stream); returns after the copies complete.  Reference counted:
+ * the device memory is released when hgks_dmesh_release has been called and
+ * every solver over the mesh destroyed.  Errors: HGKS_EINVAL, HGKS_ENOMEM,
+ * HGKS_ECUDA. */
+int hgks_dmesh_create(const hgks_mesh* mesh, void* stream, hgks_dmesh** out);
+void hgks_dmesh_release(hgks_dmesh* dmesh);
+/* what = 0 cells, 1 faces, 2 boundary ghosts, 5 device bytes of the mesh
+ * arrays, 6 and 7 device bytes of one solver's own arrays over it for
+ * precision 0 and 1, 8 solvers currently over it.  -1 for bad input. */
+int64_t hgks_dmesh_info(const hgks_dmesh* dmesh, int what);
+/* Create a solver over a device mesh: only the solver's state and work
+ * arrays are allocated (hgks_dmesh_info(., 6 | 7) bytes) and only q0 is
+ * copied.  Otherwise as hgks_init; the device mesh is not consumed. */
+int hgks_init_shared(hgks_dmesh* dmesh, const hgks_params* params, const double* q0, hgks_solver** out);
 
 /* Batched solver (no counterpart in the paper; the batching of many small
  * meshes into one launch per kernel): the n meshes form one disjoint union,
@@ -176,7 +204,8 @@ int hgks_tuning(const hgks_solver* s, int* flux_variant, int* recon_variant);
 /* Select the variants by hand (0 or 1 each); synchronises. */
 int hgks_set_tuning(hgks_solver* s, int flux_variant, int recon_variant);
 
-/* Device bytes held by the solver (its single arena), or -1. */
+/* Device bytes the solver uses (its own arrays and its device mesh, which
+ * may be shared), or -1. */
 int64_t hgks_solver_bytes(const hgks_solver* s);
 
 /* Advance n_steps S2O4 steps asynchronously on the solver's stream (Algorithm

@@ -3,9 +3,12 @@
 // kernels of hgks_kernels.cu; this file only moves data and orders launches.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -25,9 +28,21 @@ struct Member {
   std::vector<int64_t> perm;
 };
 
+// The static arrays of a (union) mesh in device memory, shared by every
+// solver created over it and freed with the last reference.
+struct hgks_dmesh {
+  hgks::HostMesh sizes;         // sizes only (no arrays)
+  std::vector<Member> members;  // one per member mesh (one for a single mesh)
+  hgks::DevMesh dm{};
+  void* arena = nullptr;
+  size_t bytes = 0;
+  std::atomic<int> refs{1};     // the creator's and one per solver
+  std::atomic<int> solvers{0};  // solvers currently over this mesh
+};
+
 struct hgks_solver {
-  hgks::HostMesh mesh;          // the mesh, or the disjoint union of a batch
-  std::vector<Member> members;
+  hgks_dmesh* mesh = nullptr;  // counted reference
+  std::vector<Member>& members() const { return mesh->members; }
   hgks::DevMesh dm{};
   hgks::DevParams dp{};
   hgks::DevWork dw{};
@@ -35,7 +50,7 @@ struct hgks_solver {
   int use_graph = 1;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  void* arena = nullptr;
+  void* arena = nullptr;  // state and work arrays, stream-ordered on `stream`
   size_t arena_bytes = 0;
   cudaGraphExec_t graph = nullptr;
   std::vector<double> hbuf;  // host staging in the internal SoA layout
@@ -200,6 +215,9 @@ int64_t hgks_mesh_info(const hgks_mesh* mesh, int what) {
     case 4: return m.M;
     case 5: return hgks::device_bytes(m, HGKS_FP64);
     case 6: return hgks::device_bytes(m, HGKS_FP32_MIXED);
+    case 7: return hgks::mesh_static_bytes(m, 1);
+    case 8: return hgks::solver_work_bytes(m, HGKS_FP64, 1);
+    case 9: return hgks::solver_work_bytes(m, HGKS_FP32_MIXED, 1);
     default: return -1;
   }
 }
@@ -208,95 +226,83 @@ int64_t hgks_mesh_info(const hgks_mesh* mesh, int what) {
 
 namespace {
 
-// Device bytes of a solver over the (union) mesh m with nmesh members.
-int64_t solver_bytes(const hgks::HostMesh& m, int precision, int nmesh) {
-  int64_t b = hgks::device_bytes(m, precision);
-  if (nmesh > 1) b += (4 * m.nc + 255) / 256 * 256;
-  b += ((int64_t)sizeof(hgks::Control) * nmesh + 255) / 256 * 256;
-  return b;
+// Device memory comes from the device's stream-ordered pool, which keeps
+// freed blocks for reuse (release threshold raised once per device): solvers
+// created and destroyed while others run allocate and free without a
+// device-wide synchronisation.
+void prepare_pool() {
+  static std::mutex mu;
+  static bool done[64] = {false};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  cudaGetLastError();
+  done[dev] = true;
 }
 
-// Build a solver over the given meshes (one, or a batch).  On HGKS_OK the
-// solver owns the meshes and the caller's handles are deleted; on failure the
-// caller's meshes are untouched.
-int create_solver(hgks_mesh* const* meshes, int n, const hgks_params* params, const double* const* q0,
-                  hgks_solver** out) {
+int alloc_on(void** p, size_t bytes, cudaStream_t st, const char* what) {
+  prepare_pool();
+  cudaError_t e = cudaMallocAsync(p, bytes, st);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    char b[200];
+    std::snprintf(b, sizeof b, "device allocation of %.3f GB for %s failed: %s", bytes / 1e9, what,
+                  cudaGetErrorString(e));
+    g_err = b;
+    return HGKS_ENOMEM;
+  }
+  return HGKS_OK;
+}
+
+void dmesh_release(hgks_dmesh* d, cudaStream_t st) {
+  if (!d || --d->refs > 0) return;
+  if (d->arena) cudaFreeAsync(d->arena, st);
+  delete d;
+}
+
+// Upload the static arrays of host mesh m (members: the member meshes in the
+// union numbering; cmesh: member of each cell when there are several) on
+// stream st.  Returns after the copies completed; the host mesh is unchanged.
+int make_dmesh(const hgks::HostMesh& m, std::vector<Member> members, const std::vector<int32_t>& cmesh,
+               cudaStream_t st, hgks_dmesh** out) {
   *out = nullptr;
-  int rc = check_params(params);
-  if (rc) return rc;
-  hgks_solver* s = nullptr;
+  hgks_dmesh* d = nullptr;
   try {
-    s = new hgks_solver;
+    d = new hgks_dmesh;
   } catch (const std::bad_alloc&) {
     return fail(HGKS_ENOMEM, "host allocation failed");
   }
+  const int n = (int)members.size();
+  d->members = std::move(members);
+  const size_t bytes = (size_t)hgks::mesh_static_bytes(m, n);
+  int rc = alloc_on(&d->arena, bytes, st, "the mesh");
+  if (rc) { delete d; return rc; }
+  d->bytes = bytes;
   auto bail = [&](int code) {
-    if (s->arena) cudaFree(s->arena);
-    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
-    if (n == 1) std::swap(meshes[0]->m, s->mesh);  // hand a single mesh back untouched
-    delete s;
+    cudaStreamSynchronize(st);
+    cudaFreeAsync(d->arena, st);
+    delete d;
     return code;
   };
-  std::vector<int32_t> cmesh;
-  try {
-    if (n == 1) {
-      std::swap(s->mesh, meshes[0]->m);
-      Member mb;
-      mb.coff = 0;
-      mb.nc = s->mesh.nc;
-      mb.perm = s->mesh.perm;
-      s->members.push_back(std::move(mb));
-    } else {
-      std::vector<const hgks::HostMesh*> parts;
-      for (int i = 0; i < n; ++i) parts.push_back(&meshes[i]->m);
-      std::vector<int64_t> coff;
-      std::string err;
-      rc = hgks::build_union(parts, s->mesh, cmesh, coff, err);
-      if (rc) { g_err = err; return bail(rc); }
-      if (!hgks::stencil_supported(s->mesh.nfc, s->mesh.K)) {
-        g_err = "batch stencil size is not among the compiled shapes";
-        return bail(HGKS_EMESH);
-      }
-      for (int i = 0; i < n; ++i) {
-        Member mb;
-        mb.coff = coff[i];
-        mb.nc = meshes[i]->m.nc;
-        mb.perm = meshes[i]->m.perm;
-        s->members.push_back(std::move(mb));
-      }
-    }
-  } catch (const std::bad_alloc&) {
-    g_err = "host allocation failed while building the batch";
-    return bail(HGKS_ENOMEM);
-  }
-  const hgks::HostMesh& m = s->mesh;
-  s->precision = params->precision;
-  s->use_graph = params->use_graph;
-  const size_t bytes = (size_t)solver_bytes(m, s->precision, n);
-  cudaError_t e = cudaMalloc(&s->arena, bytes);
-  if (e != cudaSuccess) {
-    s->arena = nullptr;
-    cudaGetLastError();
-    char b[160];
-    std::snprintf(b, sizeof b, "device allocation of %.3f GB failed: %s", bytes / 1e9, cudaGetErrorString(e));
-    g_err = b;
-    return bail(HGKS_ENOMEM);
-  }
-  s->arena_bytes = bytes;
-  if (params->stream) {
-    s->stream = static_cast<cudaStream_t>(params->stream);
-  } else {
-    e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
-    if (e != cudaSuccess) { cuda_fail(e, "cudaStreamCreate"); return bail(HGKS_ECUDA); }
-    s->own_stream = true;
-  }
-  // carve the arena
-  Carver cv{static_cast<char*>(s->arena), 0, bytes};
-  hgks::DevMesh& dm = s->dm;
+  Carver cv{static_cast<char*>(d->arena), 0, bytes};
+  hgks::DevMesh& dm = d->dm;
   dm.nc = m.nc; dm.nf = m.nf; dm.ng = m.ng; dm.nce = m.nc + m.ng; dm.ncp = m.ncp;
   dm.K = m.K; dm.M = m.M; dm.KM = m.KM; dm.G = m.G; dm.nfc = m.nfc;
   dm.nmesh = n;
-  std::vector<double> volinv(m.nc);
+  std::vector<double> volinv;
+  try {
+    volinv.resize(m.nc);
+  } catch (const std::bad_alloc&) {
+    g_err = "host allocation failed";
+    return bail(HGKS_ENOMEM);
+  }
   for (int64_t c = 0; c < m.nc; ++c) volinv[c] = 1.0 / m.vol[c];
   double* p_volinv = cv.take<double>(m.nc);
   double* p_hdt = cv.take<double>(m.nc);
@@ -318,49 +324,102 @@ int create_solver(hgks_mesh* const* meshes, int n, const hgks_params* params, co
   double* p_fdr = cv.take<double>((int64_t)m.G * 3 * m.nf);
   double* p_fn = cv.take<double>((int64_t)m.G * 3 * m.nf);
   double* p_fw = cv.take<double>((int64_t)m.G * m.nf);
-  hgks::DevWork& w = s->dw;
-  w.Q = cv.take<double>(5 * dm.nce);
-  w.Qs = cv.take<double>(5 * dm.nce);
-  w.R = cv.take<double>(5 * m.nc);
-  w.Qf = s->precision == HGKS_FP32_MIXED ? cv.take<float>(8 * dm.nce) : nullptr;
-  const int64_t rs = s->precision == HGKS_FP32_MIXED ? 4 : 8;
-  const bool f32 = s->precision == HGKS_FP32_MIXED;
-  w.coef = cv.take<char>(rs * (f32 ? hgks::kCoefRec32 : hgks::kCoefRec64) * m.nc);
-  w.Fs = cv.take<char>(rs * (f32 ? hgks::kFluxRec32 : hgks::kFluxRec64) * m.nf);
   int32_t* p_cmesh = n > 1 ? cv.take<int32_t>(m.nc) : nullptr;
-  hgks::Control* p_ctl = cv.take<hgks::Control>(n);
-  w.ctl = p_ctl;
-  if (cv.off > bytes) { g_err = "internal error: arena too small"; return bail(HGKS_ENOMEM); }
+  if (cv.off > bytes) { g_err = "internal error: mesh arena too small"; return bail(HGKS_ENOMEM); }
   dm.volinv = p_volinv; dm.hdt = p_hdt; dm.hinv = p_hinv; dm.mom = p_mom; dm.sten = p_sten; dm.pinv0 = p_pinv0;
   dm.subidx = p_subidx; dm.pinvm = p_pinvm; dm.cface = p_cface; dm.gsrc = p_gsrc; dm.gtag = p_gtag; dm.gnrm = p_gnrm;
   dm.fown = p_fown; dm.fnbr = p_fnbr; dm.fdl = p_fdl; dm.fdr = p_fdr; dm.fn = p_fn; dm.fw = p_fw;
   dm.cmesh = p_cmesh;
   cudaError_t ue = cudaSuccess;
   auto chk = [&](cudaError_t x) { if (ue == cudaSuccess) ue = x; };
-  chk(up(p_volinv, volinv, s->stream));
-  chk(up(p_hdt, m.hdt, s->stream));
-  chk(up(p_hinv, m.hinv, s->stream));
-  chk(up(p_mom, m.mom, s->stream));
-  chk(up(p_sten, m.sten, s->stream));
-  chk(up(p_pinv0, m.pinv0, s->stream));
-  chk(up(p_subidx, m.subidx, s->stream));
-  chk(up(p_pinvm, m.pinvm, s->stream));
-  chk(up(p_cface, m.cface, s->stream));
+  chk(up(p_volinv, volinv, st));
+  chk(up(p_hdt, m.hdt, st));
+  chk(up(p_hinv, m.hinv, st));
+  chk(up(p_mom, m.mom, st));
+  chk(up(p_sten, m.sten, st));
+  chk(up(p_pinv0, m.pinv0, st));
+  chk(up(p_subidx, m.subidx, st));
+  chk(up(p_pinvm, m.pinvm, st));
+  chk(up(p_cface, m.cface, st));
   if (m.ng) {
-    chk(up(p_gsrc, m.gsrc, s->stream));
-    chk(up(p_gtag, m.gtag, s->stream));
-    chk(up(p_gnrm, m.gnrm, s->stream));
+    chk(up(p_gsrc, m.gsrc, st));
+    chk(up(p_gtag, m.gtag, st));
+    chk(up(p_gnrm, m.gnrm, st));
   }
-  chk(up(p_fown, m.fown, s->stream));
-  chk(up(p_fnbr, m.fnbr, s->stream));
-  chk(up(p_fdl, m.fdl, s->stream));
-  chk(up(p_fdr, m.fdr, s->stream));
-  chk(up(p_fn, m.fn, s->stream));
-  chk(up(p_fw, m.fw, s->stream));
-  if (p_cmesh) chk(up(p_cmesh, cmesh, s->stream));
-  chk(cudaMemsetAsync(w.Q, 0, sizeof(double) * 5 * dm.nce, s->stream));
-  chk(cudaMemsetAsync(w.Qs, 0, sizeof(double) * 5 * dm.nce, s->stream));
+  chk(up(p_fown, m.fown, st));
+  chk(up(p_fnbr, m.fnbr, st));
+  chk(up(p_fdl, m.fdl, st));
+  chk(up(p_fdr, m.fdr, st));
+  chk(up(p_fn, m.fn, st));
+  chk(up(p_fw, m.fw, st));
+  if (p_cmesh) chk(up(p_cmesh, cmesh, st));
+  if (ue == cudaSuccess) ue = cudaStreamSynchronize(st);  // the host arrays may go away after return
   if (ue != cudaSuccess) { cuda_fail(ue, "uploading the mesh"); return bail(HGKS_ECUDA); }
+  d->sizes.ctype = m.ctype; d->sizes.nfc = m.nfc; d->sizes.G = m.G; d->sizes.M = m.M; d->sizes.KM = m.KM;
+  d->sizes.K = m.K; d->sizes.nc = m.nc; d->sizes.nf = m.nf; d->sizes.ng = m.ng; d->sizes.ncp = m.ncp;
+  *out = d;
+  return HGKS_OK;
+}
+
+// The solver's stream: the caller's, or a new non-blocking one.
+int solver_stream(const hgks_params* params, cudaStream_t* st, bool* own) {
+  if (params->stream) {
+    *st = static_cast<cudaStream_t>(params->stream);
+    *own = false;
+    return HGKS_OK;
+  }
+  cudaError_t e = cudaStreamCreateWithFlags(st, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+  *own = true;
+  return HGKS_OK;
+}
+
+// Create a solver over device mesh d (takes a new reference on success) on
+// stream st (owned when own): allocate the state and work arrays, set the
+// parameters, copy the initial states q0[i] of the members, compute the first
+// step bound and, when asked, time the kernel variants.
+int make_solver(hgks_dmesh* d, const hgks_params* params, const double* const* q0, cudaStream_t st, bool own,
+                hgks_solver** out) {
+  *out = nullptr;
+  hgks_solver* s = nullptr;
+  try {
+    s = new hgks_solver;
+  } catch (const std::bad_alloc&) {
+    return fail(HGKS_ENOMEM, "host allocation failed");
+  }
+  s->stream = st;
+  s->own_stream = own;
+  auto bail = [&](int code) {
+    if (s->arena) {
+      cudaStreamSynchronize(s->stream);
+      cudaFreeAsync(s->arena, s->stream);
+    }
+    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+    return code;
+  };
+  const int n = (int)d->members.size();
+  const hgks::HostMesh& m = d->sizes;
+  s->precision = params->precision;
+  s->use_graph = params->use_graph;
+  const size_t bytes = (size_t)hgks::solver_work_bytes(m, s->precision, n);
+  int rc = alloc_on(&s->arena, bytes, s->stream, "the solver state");
+  if (rc) return bail(rc);
+  s->arena_bytes = bytes;
+  s->dm = d->dm;
+  const hgks::DevMesh& dm = s->dm;
+  Carver cv{static_cast<char*>(s->arena), 0, bytes};
+  hgks::DevWork& w = s->dw;
+  const bool f32 = s->precision == HGKS_FP32_MIXED;
+  const int64_t rs = f32 ? 4 : 8;
+  w.Q = cv.take<double>(5 * dm.nce);
+  w.Qs = cv.take<double>(5 * dm.nce);
+  w.R = cv.take<double>(5 * m.nc);
+  w.Qf = f32 ? cv.take<float>(8 * dm.nce) : nullptr;
+  w.coef = cv.take<char>(rs * (f32 ? hgks::kCoefRec32 : hgks::kCoefRec64) * m.nc);
+  w.Fs = cv.take<char>(rs * (f32 ? hgks::kFluxRec32 : hgks::kFluxRec64) * m.nf);
+  w.ctl = cv.take<hgks::Control>(n);
+  if (cv.off > bytes) { g_err = "internal error: solver arena too small"; return bail(HGKS_ENOMEM); }
   // parameters
   hgks::DevParams& dp = s->dp;
   dp.gamma = params->gamma;
@@ -379,10 +438,17 @@ int create_solver(hgks_mesh* const* meshes, int n, const hgks_params* params, co
   dp.flux_variant = 0;
   dp.recon_variant = 0;
   hgks::prepare_kernels(dm, s->precision);
-  // initial states
-  s->hbuf.assign(5 * dm.nce, 0.0);
-  for (int i = 0; i < n; ++i) to_internal(s->members[i], q0[i], s->hbuf, dm.nce);
-  e = cudaMemcpyAsync(w.Q, s->hbuf.data(), sizeof(double) * 5 * dm.nce, cudaMemcpyHostToDevice, s->stream);
+  // initial states (the ghost slots and Q* start at zero)
+  try {
+    s->hbuf.assign(5 * dm.nce, 0.0);
+  } catch (const std::bad_alloc&) {
+    g_err = "host allocation failed";
+    return bail(HGKS_ENOMEM);
+  }
+  for (int i = 0; i < n; ++i) to_internal(d->members[i], q0[i], s->hbuf, dm.nce);
+  cudaError_t e = cudaMemsetAsync(w.Qs, 0, sizeof(double) * 5 * dm.nce, s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(w.Q, s->hbuf.data(), sizeof(double) * 5 * dm.nce, cudaMemcpyHostToDevice, s->stream);
   if (e != cudaSuccess) { cuda_fail(e, "copying the initial state"); return bail(HGKS_ECUDA); }
   hgks::launch_reset(dm, dp, w, s->precision, -1, 0.0, s->stream);
   e = cudaStreamSynchronize(s->stream);
@@ -409,20 +475,75 @@ int create_solver(hgks_mesh* const* meshes, int n, const hgks_params* params, co
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) { cuda_fail(e, "autotuning"); return bail(HGKS_ECUDA); }
   }
-  for (int i = 0; i < n; ++i) delete meshes[i];
-  // the device holds the mesh now; keep only the sizes on the host
-  {
-    hgks::HostMesh sizes;
-    sizes.ctype = m.ctype; sizes.nfc = m.nfc; sizes.G = m.G; sizes.M = m.M; sizes.KM = m.KM; sizes.K = m.K;
-    sizes.nc = m.nc; sizes.nf = m.nf; sizes.ng = m.ng; sizes.ncp = m.ncp;
-    s->mesh = std::move(sizes);
+  ++d->refs;
+  ++d->solvers;
+  s->mesh = d;
+  *out = s;
+  return HGKS_OK;
+}
+
+// hgks_init / hgks_batch_init: upload the (union) mesh, then create the
+// solver over it; on success the solver holds the only reference to the
+// device mesh and the caller's host meshes are deleted, on failure they are
+// untouched.
+int create_solver(hgks_mesh* const* meshes, int n, const hgks_params* params, const double* const* q0,
+                  hgks_solver** out) {
+  *out = nullptr;
+  int rc = check_params(params);
+  if (rc) return rc;
+  cudaStream_t st = nullptr;
+  bool own = false;
+  rc = solver_stream(params, &st, &own);
+  if (rc) return rc;
+  auto drop_stream = [&]() { if (own) cudaStreamDestroy(st); };
+  hgks_dmesh* d = nullptr;
+  try {
+    if (n == 1) {
+      const hgks::HostMesh& m = meshes[0]->m;
+      std::vector<Member> mbs(1);
+      mbs[0].coff = 0;
+      mbs[0].nc = m.nc;
+      mbs[0].perm = m.perm;
+      rc = make_dmesh(m, std::move(mbs), {}, st, &d);
+    } else {
+      std::vector<const hgks::HostMesh*> parts;
+      for (int i = 0; i < n; ++i) parts.push_back(&meshes[i]->m);
+      hgks::HostMesh u;
+      std::vector<int32_t> cmesh;
+      std::vector<int64_t> coff;
+      std::string err;
+      rc = hgks::build_union(parts, u, cmesh, coff, err);
+      if (rc) g_err = err;
+      if (!rc && !hgks::stencil_supported(u.nfc, u.K)) {
+        g_err = "batch stencil size is not among the compiled shapes";
+        rc = HGKS_EMESH;
+      }
+      if (!rc) {
+        std::vector<Member> mbs(n);
+        for (int i = 0; i < n; ++i) {
+          mbs[i].coff = coff[i];
+          mbs[i].nc = meshes[i]->m.nc;
+          mbs[i].perm = meshes[i]->m.perm;
+        }
+        rc = make_dmesh(u, std::move(mbs), cmesh, st, &d);
+      }
+    }
+  } catch (const std::bad_alloc&) {
+    g_err = "host allocation failed while preparing the mesh";
+    rc = HGKS_ENOMEM;
   }
+  if (rc) { drop_stream(); return rc; }
+  hgks_solver* s = nullptr;
+  rc = make_solver(d, params, q0, st, own, &s);  // destroys an owned stream on failure
+  dmesh_release(d, rc ? nullptr : st);           // the solver holds its own reference
+  if (rc) return rc;
+  for (int i = 0; i < n; ++i) delete meshes[i];
   *out = s;
   return HGKS_OK;
 }
 
 int read_flags(hgks_solver* s, int only, hgks::Control* first) {
-  std::vector<hgks::Control> c(s->members.size());
+  std::vector<hgks::Control> c(s->members().size());
   HGKS_CUDA(cudaMemcpy(c.data(), s->dw.ctl, sizeof(hgks::Control) * c.size(), cudaMemcpyDeviceToHost),
             "reading the control blocks");
   if (first) *first = c[only >= 0 ? only : 0];
@@ -453,16 +574,16 @@ int hgks_batch_init(hgks_mesh* const* meshes, int n, const hgks_params* params, 
   return create_solver(meshes, n, params, q0, out);
 }
 
-int hgks_members(const hgks_solver* s) { return s ? (int)s->members.size() : -1; }
+int hgks_members(const hgks_solver* s) { return s ? (int)s->members().size() : -1; }
 
 int hgks_member_write(hgks_solver* s, int member, const double* q, double t) {
   if (!s || !q) return fail(HGKS_EINVAL, "NULL argument");
-  if (member < 0 || member >= (int)s->members.size()) return fail(HGKS_EINVAL, "member out of range");
+  if (member < 0 || member >= (int)s->members().size()) return fail(HGKS_EINVAL, "member out of range");
   HGKS_CUDA(cudaStreamSynchronize(s->stream), "waiting for queued work");
   s->hbuf.resize(5 * s->dm.nce);
   HGKS_CUDA(cudaMemcpy(s->hbuf.data(), s->dw.Q, sizeof(double) * 5 * s->dm.nce, cudaMemcpyDeviceToHost),
             "reading the state");
-  to_internal(s->members[member], q, s->hbuf, s->dm.nce);
+  to_internal(s->members()[member], q, s->hbuf, s->dm.nce);
   HGKS_CUDA(cudaMemcpyAsync(s->dw.Q, s->hbuf.data(), sizeof(double) * 5 * s->dm.nce, cudaMemcpyHostToDevice, s->stream),
             "copying the state");
   hgks::launch_reset(s->dm, s->dp, s->dw, s->precision, member, t, s->stream);
@@ -520,13 +641,13 @@ int hgks_sync(hgks_solver* s) {
 
 int hgks_member_read(hgks_solver* s, int member, double* q_out, double* t_out, int64_t* steps_out) {
   if (!s) return fail(HGKS_EINVAL, "NULL solver");
-  if (member < 0 || member >= (int)s->members.size()) return fail(HGKS_EINVAL, "member out of range");
+  if (member < 0 || member >= (int)s->members().size()) return fail(HGKS_EINVAL, "member out of range");
   HGKS_CUDA(cudaStreamSynchronize(s->stream), "synchronising");
   if (q_out) {
     s->hbuf.resize(5 * s->dm.nce);
     HGKS_CUDA(cudaMemcpy(s->hbuf.data(), s->dw.Q, sizeof(double) * 5 * s->dm.nce, cudaMemcpyDeviceToHost),
               "reading the state");
-    to_caller(s->members[member], s->hbuf.data(), s->dm.nce, q_out);
+    to_caller(s->members()[member], s->hbuf.data(), s->dm.nce, q_out);
   }
   hgks::Control c;
   const int rc = read_flags(s, member, &c);
@@ -542,7 +663,7 @@ int hgks_read(hgks_solver* s, double* q_out, double* t_out, int64_t* steps_out) 
 int hgks_stage_operator(hgks_solver* s, double dt, double* L_out, double* dL_out) {
   if (!s || !L_out || !dL_out) return fail(HGKS_EINVAL, "NULL argument");
   if (!(dt > 0.0)) return fail(HGKS_EINVAL, "dt must be positive");
-  if (s->members.size() != 1) return fail(HGKS_EINVAL, "the stage operator is defined for single-mesh solvers");
+  if (s->members().size() != 1) return fail(HGKS_EINVAL, "the stage operator is defined for single-mesh solvers");
   const int64_t nc = s->dm.nc;
   // the stage buffers Q* and R are free between steps
   hgks::launch_operator(s->dm, s->dp, s->dw, s->precision, dt, s->dw.Qs, s->dw.R, s->stream);
@@ -550,9 +671,9 @@ int hgks_stage_operator(hgks_solver* s, double dt, double* L_out, double* dL_out
   HGKS_CUDA(cudaGetLastError(), "evaluating the stage operator");
   std::vector<double> h(5 * nc);
   HGKS_CUDA(cudaMemcpy(h.data(), s->dw.Qs, sizeof(double) * 5 * nc, cudaMemcpyDeviceToHost), "reading L");
-  to_caller(s->members[0], h.data(), nc, L_out);
+  to_caller(s->members()[0], h.data(), nc, L_out);
   HGKS_CUDA(cudaMemcpy(h.data(), s->dw.R, sizeof(double) * 5 * nc, cudaMemcpyDeviceToHost), "reading dL/dt");
-  to_caller(s->members[0], h.data(), nc, dL_out);
+  to_caller(s->members()[0], h.data(), nc, dL_out);
   return HGKS_OK;
 }
 
@@ -579,7 +700,7 @@ int hgks_profile(hgks_solver* s, int n_steps, double t_end, double dt_fixed, dou
   return rc;
 }
 
-int64_t hgks_solver_bytes(const hgks_solver* s) { return s ? (int64_t)s->arena_bytes : -1; }
+int64_t hgks_solver_bytes(const hgks_solver* s) { return s ? (int64_t)(s->arena_bytes + s->mesh->bytes) : -1; }
 
 int hgks_set_tuning(hgks_solver* s, int flux_variant, int recon_variant) {
   if (!s) return fail(HGKS_EINVAL, "NULL solver");
@@ -606,9 +727,65 @@ void hgks_destroy(hgks_solver* s) {
   if (!s) return;
   if (s->stream) cudaStreamSynchronize(s->stream);
   if (s->graph) cudaGraphExecDestroy(s->graph);
-  if (s->arena) cudaFree(s->arena);
+  if (s->arena) cudaFreeAsync(s->arena, s->stream);
+  --s->mesh->solvers;
+  dmesh_release(s->mesh, s->stream);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
   delete s;
+}
+
+int hgks_dmesh_create(const hgks_mesh* mesh, void* stream, hgks_dmesh** out) {
+  if (!mesh || !out) return fail(HGKS_EINVAL, "NULL argument");
+  *out = nullptr;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  bool own = false;
+  if (!st) {
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+    own = true;
+  }
+  int rc;
+  try {
+    const hgks::HostMesh& m = mesh->m;
+    std::vector<Member> mbs(1);
+    mbs[0].coff = 0;
+    mbs[0].nc = m.nc;
+    mbs[0].perm = m.perm;
+    rc = make_dmesh(m, std::move(mbs), {}, st, out);
+  } catch (const std::bad_alloc&) {
+    rc = fail(HGKS_ENOMEM, "host allocation failed");
+  }
+  if (own) cudaStreamDestroy(st);
+  return rc;
+}
+
+void hgks_dmesh_release(hgks_dmesh* dmesh) { dmesh_release(dmesh, nullptr); }
+
+int64_t hgks_dmesh_info(const hgks_dmesh* d, int what) {
+  if (!d) return -1;
+  switch (what) {
+    case 0: return d->sizes.nc;
+    case 1: return d->sizes.nf;
+    case 2: return d->sizes.ng;
+    case 5: return (int64_t)d->bytes;
+    case 6: return hgks::solver_work_bytes(d->sizes, HGKS_FP64, (int)d->members.size());
+    case 7: return hgks::solver_work_bytes(d->sizes, HGKS_FP32_MIXED, (int)d->members.size());
+    case 8: return d->solvers.load();
+    default: return -1;
+  }
+}
+
+int hgks_init_shared(hgks_dmesh* dmesh, const hgks_params* params, const double* q0, hgks_solver** out) {
+  if (!dmesh || !out || !q0) return fail(HGKS_EINVAL, "NULL argument");
+  *out = nullptr;
+  int rc = check_params(params);
+  if (rc) return rc;
+  cudaStream_t st = nullptr;
+  bool own = false;
+  rc = solver_stream(params, &st, &own);
+  if (rc) return rc;
+  const double* q[1] = {q0};
+  return make_solver(dmesh, params, q, st, own, out);
 }
 
 }  // extern "C"

@@ -737,14 +737,12 @@ int build_union(const std::vector<const HostMesh*>& parts, HostMesh& u, std::vec
   return HGKS_OK;
 }
 
-int64_t device_bytes(const HostMesh& m, int precision) {
+int64_t mesh_static_bytes(const HostMesh& m, int nmesh) {
   auto al = [](int64_t b) { return (b + 255) / 256 * 256; };
-  const int64_t nc = m.nc, nf = m.nf, ng = m.ng, nce = nc + ng, ncp = m.ncp;
-  const int64_t rs = precision == HGKS_FP32_MIXED ? 4 : 8;
+  const int64_t nc = m.nc, nf = m.nf, ng = m.ng, ncp = m.ncp;
   int64_t b = 0;
-  // static mesh data
-  b += al(8 * nc) * 4;                         // vol, hdt, hinv, (spare)
-  b += al(8 * 3 * nc) + al(8 * 6 * nc);        // cen, mom
+  b += al(8 * nc) * 4;                         // volinv, hdt, hinv, (spare)
+  b += al(8 * 3 * nc) + al(8 * 6 * nc);        // (centroid slot), mom
   b += al(4 * (int64_t)m.K * nc);              // sten
   b += al(8 * (int64_t)9 * m.K * ncp);         // pinv0
   b += al((int64_t)m.M * m.KM * ncp);          // subidx
@@ -753,15 +751,27 @@ int64_t device_bytes(const HostMesh& m, int precision) {
   b += al(4 * ng) * 2 + al(8 * 3 * ng);        // ghosts
   b += al(4 * nf) * 2;                         // fown, fnbr
   b += al(8 * (int64_t)m.G * 3 * nf) * 3 + al(8 * (int64_t)m.G * nf);  // fdl fdr fn fw
-  // state and work arrays
+  if (nmesh > 1) b += al(4 * nc);              // member of each cell
+  return b + 256;
+}
+
+int64_t solver_work_bytes(const HostMesh& m, int precision, int nmesh) {
+  auto al = [](int64_t b) { return (b + 255) / 256 * 256; };
+  const int64_t nc = m.nc, nf = m.nf, nce = nc + m.ng;
+  const bool f32 = precision == HGKS_FP32_MIXED;
+  const int64_t rs = f32 ? 4 : 8;
+  int64_t b = 0;
   b += al(8 * 5 * nce) * 2;                    // Q, Q* (with ghost slots)
   b += al(8 * 5 * nc);                         // R (partial S2O4 sum)
-  if (precision == HGKS_FP32_MIXED) b += al(4 * 8 * nce);  // binary32 copy of the stage state, 32 B per cell
-  const bool f32 = precision == HGKS_FP32_MIXED;
+  if (f32) b += al(4 * 8 * nce);               // binary32 copy of the stage state, 32 B per cell
   b += al(rs * (f32 ? kCoefRec32 : kCoefRec64) * nc);  // reconstruction coefficients
   b += al(rs * (f32 ? kFluxRec32 : kFluxRec64) * nf);  // face flux and its time slope
-  b += 4096;                                   // control block
-  return b;
+  b += al((int64_t)sizeof(Control) * nmesh);  // control blocks
+  return b + 256;
+}
+
+int64_t device_bytes(const HostMesh& m, int precision) {
+  return mesh_static_bytes(m, 1) + solver_work_bytes(m, precision, 1);
 }
 
 }  // namespace hgks

@@ -68,8 +68,11 @@ int build_host_mesh(const hgks_mesh_desc& d, HostMesh& m, std::string& err);
 int build_union(const std::vector<const HostMesh*>& parts, HostMesh& u, std::vector<int32_t>& cmesh,
                 std::vector<int64_t>& coff, std::string& err);
 
-// Device bytes a solver for this mesh allocates (precision HGKS_FP64 or
-// HGKS_FP32_MIXED), including alignment padding.
+// Device bytes, including alignment padding, of the static mesh arrays (a
+// device mesh over nmesh members), of one solver's state and work arrays
+// (precision HGKS_FP64 or HGKS_FP32_MIXED), and of both for a single mesh.
+int64_t mesh_static_bytes(const HostMesh& m, int nmesh);
+int64_t solver_work_bytes(const HostMesh& m, int precision, int nmesh);
 int64_t device_bytes(const HostMesh& m, int precision);
 
 }  // namespace hgks

@@ -62,7 +62,8 @@ EXPORTS = ("hgks_params_default", "hgks_mesh_create", "hgks_mesh_destroy", "hgks
            "hgks_init",
            "hgks_batch_init", "hgks_members", "hgks_write", "hgks_member_write", "hgks_step", "hgks_query",
            "hgks_sync", "hgks_read", "hgks_member_read", "hgks_stage_operator", "hgks_profile", "hgks_solver_bytes",
-           "hgks_tuning", "hgks_set_tuning", "hgks_destroy", "hgks_last_error", "hgks_cfl_dt_noalloc")
+           "hgks_tuning", "hgks_set_tuning", "hgks_destroy", "hgks_last_error", "hgks_cfl_dt_noalloc",
+           "hgks_dmesh_create", "hgks_dmesh_release", "hgks_dmesh_info", "hgks_init_shared")
 
 
 def lib():
@@ -105,6 +106,14 @@ def lib():
             L.hgks_profile.argtypes = [vp, C.c_int, C.c_double, C.c_double, dp]
             L.hgks_cfl_dt_noalloc.argtypes = [vp, vp, C.c_int64, C.POINTER(hgks_params), vp, vp]
             L.hgks_cfl_dt_noalloc.restype = C.c_int
+            L.hgks_dmesh_create.argtypes = [vp, vp, C.POINTER(vp)]
+            L.hgks_dmesh_create.restype = C.c_int
+            L.hgks_dmesh_release.argtypes = [vp]
+            L.hgks_dmesh_release.restype = None
+            L.hgks_dmesh_info.argtypes = [vp, C.c_int]
+            L.hgks_dmesh_info.restype = C.c_int64
+            L.hgks_init_shared.argtypes = [vp, C.POINTER(hgks_params), dp, C.POINTER(vp)]
+            L.hgks_init_shared.restype = C.c_int
             L.hgks_destroy.argtypes = [vp]
             L.hgks_destroy.restype = None
             L.hgks_last_error.restype = C.c_char_p
@@ -208,6 +217,15 @@ class Mesh:
     def device_bytes(self, precision: int = HGKS_FP64) -> int:
         return self.info(5 if precision == HGKS_FP64 else 6)
 
+    @property
+    def static_bytes(self) -> int:
+        """Device bytes of the mesh arrays alone (a DeviceMesh)."""
+        return self.info(7)
+
+    def work_bytes(self, precision: int = HGKS_FP64) -> int:
+        """Device bytes of one solver's own arrays over a DeviceMesh."""
+        return self.info(8 if precision == HGKS_FP64 else 9)
+
     def geometry(self):
         """(cell volumes, 3|cell|/|surface|) in caller order."""
         vol = np.empty(self.n_cells)
@@ -236,14 +254,55 @@ class Mesh:
             self._h = None
 
 
+class DeviceMesh:
+    """hgks_dmesh_create / hgks_dmesh_release: a mesh resident in device
+    memory, shared by the solvers created over it (Solver(dmesh, q0, ...))."""
+
+    def __init__(self, mesh: Mesh, stream: int = 0):
+        h = C.c_void_p()
+        _check(lib().hgks_dmesh_create(mesh._h, C.c_void_p(stream or None), C.byref(h)), "hgks_dmesh_create")
+        self._h = h
+
+    def info(self, what: int) -> int:
+        return int(lib().hgks_dmesh_info(self._h, what))
+
+    @property
+    def n_cells(self):
+        return self.info(0)
+
+    @property
+    def bytes(self) -> int:
+        return self.info(5)
+
+    def work_bytes(self, precision: int = HGKS_FP64) -> int:
+        return self.info(6 if precision == HGKS_FP64 else 7)
+
+    @property
+    def solvers(self) -> int:
+        return self.info(8)
+
+    def release(self):
+        h, self._h = getattr(self, "_h", None), None
+        if h:
+            lib().hgks_dmesh_release(h)
+
+    def __del__(self):
+        self.release()
+
+
 class Solver:
-    """hgks_init / hgks_step / hgks_read / hgks_destroy on one mesh, or
-    hgks_batch_init on a list of meshes (one launch per kernel for all)."""
+    """hgks_init / hgks_step / hgks_read / hgks_destroy on one mesh,
+    hgks_batch_init on a list of meshes (one launch per kernel for all), or
+    hgks_init_shared on a DeviceMesh (the mesh is not consumed)."""
 
     def __init__(self, mesh, q0, params: hgks_params | None = None, **kw):
         p = params if params is not None else make_params(**kw)
         h = C.c_void_p()
-        if isinstance(mesh, (list, tuple)):
+        if isinstance(mesh, DeviceMesh):
+            self.member_cells = [mesh.n_cells]
+            q0 = np.ascontiguousarray(q0, dtype=np.float64).reshape(mesh.n_cells, 5)
+            _check(lib().hgks_init_shared(mesh._h, C.byref(p), _dp(q0), C.byref(h)), "hgks_init_shared")
+        elif isinstance(mesh, (list, tuple)):
             meshes = list(mesh)
             self.member_cells = [m.n_cells for m in meshes]
             qs = [np.ascontiguousarray(q, dtype=np.float64).reshape(n, 5) for q, n in zip(q0, self.member_cells)]

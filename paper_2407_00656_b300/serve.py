@@ -3,10 +3,17 @@
 Requests (a mesh, an initial state, physical parameters and a step count)
 arrive over time.  The loop
   * admits waiting requests in arrival order while their device bytes fit the
-    memory budget (hgks_mesh_info / hgks_solver_bytes),
-  * packs small requests that share their parameters and arrive together
-    into one batched solver (hgks_batch_init: one launch per kernel for all
-    of them),
+    memory budget: a solver's own state and work arrays, plus the static
+    mesh arrays when its geometry is not yet resident,
+  * keeps one device mesh per geometry resident (hgks_dmesh_create) and
+    creates every large request's solver over it (hgks_init_shared: only the
+    state and work arrays are allocated, only the initial state is copied),
+    evicting device meshes that no solve uses when memory is short,
+  * packs small requests that share their parameters and step count and wait
+    together into one batched solver (hgks_batch_init: one launch per kernel
+    for all of them), up to a total cell count,
+  * creates solvers on a worker thread, so that solver set-up (host work and
+    copies) overlaps the steps of the solves already running,
   * keeps every admitted solve resident on the device, each solver on its own
     CUDA stream, and interleaves their steps in chunks: a chunk is queued
     whenever a solver's previous chunk has finished (hgks_query), so work of
@@ -15,14 +22,17 @@ arrive over time.  The loop
   * reads a finished solve back, frees its memory and records its latency
     (completion time minus arrival time).
 
-All numerics run in libhgks; this module only schedules.  Built meshes are
-cached by geometry and cloned per request (hgks_mesh_clone), the warm-cache
-case of a service that sees the same geometries repeatedly.
+All numerics run in libhgks; this module only schedules.  Built host meshes
+are cached by geometry (the warm-cache case of a service that sees the same
+geometries repeatedly).
 """
 from __future__ import annotations
 
 import math
+import threading
 import time
+from collections import OrderedDict
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -62,29 +72,32 @@ def sphere_params(re: float, mach: float = 0.2535):
 
 
 class MeshCache:
-    """Built meshes and initial states by geometry key, cloned per request."""
+    """Built host meshes and initial states by geometry key."""
 
     def __init__(self):
         self._m = {}
+        self._lock = threading.Lock()
 
     def get(self, kind: str, size: int):
+        """A copy of the cached mesh (for a solver that consumes it) and the state."""
         mesh, q = self.peek(kind, size)
         return mesh.clone(), q
 
     def peek(self, kind: str, size: int):
         """The cached mesh itself (not a copy) and its initial state."""
         key = (kind, size)
-        if key not in self._m:
-            if kind == "density":
-                xyz, cells, per = I.kuhn_cube(size, jitter=0.15, seed=size)
-                mesh = H.Mesh(xyz, cells, per)
-                q = I.density_wave_state(xyz, cells, 0.0)
-            else:
-                xyz, cells, bfn, bft = I.sphere_shell(size, sphere_layers(size), seed=size)
-                mesh = H.Mesh(xyz, cells, None, bfn, bft)
-                q = np.tile(I.free_stream(0.2535), (len(cells), 1))
-            self._m[key] = (mesh, q)
-        return self._m[key]
+        with self._lock:
+            if key not in self._m:
+                if kind == "density":
+                    xyz, cells, per = I.kuhn_cube(size, jitter=0.15, seed=size)
+                    mesh = H.Mesh(xyz, cells, per)
+                    q = I.density_wave_state(xyz, cells, 0.0)
+                else:
+                    xyz, cells, bfn, bft = I.sphere_shell(size, sphere_layers(size), seed=size)
+                    mesh = H.Mesh(xyz, cells, None, bfn, bft)
+                    q = np.tile(I.free_stream(0.2535), (len(cells), 1))
+                self._m[key] = (mesh, q)
+            return self._m[key]
 
     def warm(self, requests):
         for r in requests:
@@ -97,16 +110,19 @@ class _Slot:
     reqs: list
     remaining: int
     bytes: int
+    key: tuple | None  # geometry of a shared device mesh, None for a batch
 
 
 class Server:
     def __init__(self, mem_budget: int, precision: int = H.HGKS_FP32_MIXED, chunk_steps: int = 10,
-                 small_cells: int = 100_000, max_batch: int = 16, cache: MeshCache | None = None):
+                 small_cells: int = 60_000, max_batch: int = 16, batch_cells: int = 300_000,
+                 cache: MeshCache | None = None):
         self.mem_budget = int(mem_budget)
         self.precision = precision
         self.chunk = chunk_steps
         self.small = small_cells
         self.max_batch = max_batch
+        self.batch_cells = batch_cells
         self.cache = cache or MeshCache()
 
     def _params_key(self, r: Request):
@@ -116,75 +132,151 @@ class Server:
         """Serve the requests (list of Request, arrival times relative to the
         start); returns them with admitted/finished/result filled in."""
         pending = sorted(requests, key=lambda r: r.arrival)
-        queue, active = [], []
+        queue, active, creating = [], [], []
+        dev = OrderedDict()   # geometry -> DeviceMesh, least recently used first
+        dev_bytes = {}        # geometry -> device bytes of its mesh (resident or being created)
+        inuse = {}            # geometry -> admitted solves that use its device mesh
+        dev_lock = threading.Lock()
         used = 0
         self.peak_used = 0
         self.peak_active = 0
+        worker = ThreadPoolExecutor(max_workers=1)
         t0 = time.perf_counter()
-        pi = 0
-        while pi < len(pending) or queue or active:
-            now = time.perf_counter() - t0
-            if now > time_limit:
-                raise TimeoutError("serving run exceeded its time limit")
-            while pi < len(pending) and pending[pi].arrival <= now:
-                queue.append(pending[pi])
-                pi += 1
-            busy = False
-            # admission in arrival order while memory allows
-            while queue:
-                head = queue[0]
-                mesh, q = self.cache.peek(head.kind, head.size)
-                group = [(head, mesh, q)]
-                if mesh.n_cells < self.small:
-                    key = (head.kind, self._params_key(head), head.steps)
-                    for r in queue[1:]:
-                        if len(group) >= self.max_batch:
-                            break
-                        if (r.kind, self._params_key(r), r.steps) == key:
-                            m2, q2 = self.cache.peek(r.kind, r.size)
-                            if m2.n_cells < self.small:
-                                group.append((r, m2, q2))
-                need = sum(m.device_bytes(self.precision) for _, m, _ in group) + 65536 * len(group)
-                if used + need > self.mem_budget:
-                    if not active:
-                        raise MemoryError(f"request {head.rid} needs {need} bytes, budget {self.mem_budget}")
-                    break
-                meshes = [m.clone() for _, m, _ in group]
-                states = [qq for _, _, qq in group]
-                solver = H.Solver(meshes if len(group) > 1 else meshes[0], states if len(group) > 1 else states[0],
-                                  precision=self.precision, **head.params)
-                nb = solver.device_bytes
-                used += nb
-                tnow = time.perf_counter() - t0
-                for r, m, _ in group:
-                    r.admitted = tnow
-                    queue.remove(r)
-                for i, (r, _, _) in enumerate(group):
-                    r.cells = solver.member_cells[i]
-                active.append(_Slot(solver, [r for r, _, _ in group], head.steps, nb))
-                self.peak_used = max(self.peak_used, used)
-                self.peak_active = max(self.peak_active, len(active))
-                busy = True
-            # queue the next chunk of every idle solve
-            for sl in active:
-                if sl.remaining > 0 and sl.solver.query():
-                    k = min(self.chunk, sl.remaining)
-                    sl.solver.step(k)
-                    sl.remaining -= k
-                    busy = True
-            # collect finished solves
-            for sl in list(active):
-                if sl.remaining == 0 and sl.solver.query():
+
+        def create_shared(key, mesh, q, params):
+            with dev_lock:
+                dm = dev.get(key)
+            if dm is None:
+                dm = H.DeviceMesh(mesh)
+                with dev_lock:
+                    dev[key] = dm
+            return H.Solver(dm, q, precision=self.precision, **params)
+
+        def create_batch(meshes, states, params):
+            return H.Solver([m.clone() for m in meshes], states, precision=self.precision, **params)
+
+        def evict(need):
+            """Release idle device meshes (least recently used first) until
+            `need` more bytes fit; returns the bytes freed."""
+            freed = 0
+            with dev_lock:
+                for key in list(dev.keys()):
+                    if used - freed + need <= self.mem_budget:
+                        break
+                    if inuse.get(key, 0) == 0:
+                        dev.pop(key).release()
+                        freed += dev_bytes.pop(key)
+            return freed
+
+        try:
+            pi = 0
+            while pi < len(pending) or queue or active or creating:
+                now = time.perf_counter() - t0
+                if now > time_limit:
+                    raise TimeoutError("serving run exceeded its time limit")
+                while pi < len(pending) and pending[pi].arrival <= now:
+                    queue.append(pending[pi])
+                    pi += 1
+                busy = False
+                # admission in arrival order while memory allows
+                while queue:
+                    head = queue[0]
+                    mesh, q = self.cache.peek(head.kind, head.size)
+                    if mesh.n_cells < self.small:
+                        group = [(head, mesh, q)]
+                        key = (head.kind, self._params_key(head), head.steps)
+                        total = mesh.n_cells
+                        for r in queue[1:]:
+                            if len(group) >= self.max_batch:
+                                break
+                            if (r.kind, self._params_key(r), r.steps) == key:
+                                m2, q2 = self.cache.peek(r.kind, r.size)
+                                if m2.n_cells < self.small and total + m2.n_cells <= self.batch_cells:
+                                    group.append((r, m2, q2))
+                                    total += m2.n_cells
+                        need = sum(m.device_bytes(self.precision) for _, m, _ in group) + 65536 * len(group)
+                        gkey = None
+                    else:
+                        group = [(head, mesh, q)]
+                        gkey = (head.kind, head.size)
+                        need = mesh.work_bytes(self.precision)
+                        if gkey not in dev_bytes:
+                            need += mesh.static_bytes
+                    if used + need > self.mem_budget:
+                        used -= evict(need)
+                    if used + need > self.mem_budget:
+                        if not active and not creating:
+                            raise MemoryError(f"request {head.rid} needs {need} bytes, budget {self.mem_budget}")
+                        break
                     tnow = time.perf_counter() - t0
-                    for i, r in enumerate(sl.reqs):
-                        r.result, r.t, r.steps_done = sl.solver.member_read(i)
-                        r.finished = tnow
-                    sl.solver.close()
-                    used -= sl.bytes
-                    active.remove(sl)
+                    for r, m, _ in group:
+                        r.admitted = tnow
+                        queue.remove(r)
+                    if gkey is None:
+                        fut = worker.submit(create_batch, [m for _, m, _ in group], [qq for _, _, qq in group],
+                                            head.params)
+                        used += need
+                        creating.append((fut, [r for r, _, _ in group], need, 0, None))
+                    else:
+                        if gkey not in dev_bytes:
+                            dev_bytes[gkey] = mesh.static_bytes
+                        inuse[gkey] = inuse.get(gkey, 0) + 1
+                        work = mesh.work_bytes(self.precision)
+                        used += need
+                        fut = worker.submit(create_shared, gkey, mesh, q, head.params)
+                        creating.append((fut, [head], work, 0, gkey))
+                    self.peak_used = max(self.peak_used, used)
                     busy = True
-            if not busy:
-                time.sleep(0.0002)
+                # solvers that finished their set-up start stepping
+                for item in list(creating):
+                    fut, reqs, nb, _, gkey = item
+                    if not fut.done():
+                        continue
+                    creating.remove(item)
+                    solver = fut.result()  # a creation error ends the run
+                    if gkey is None:
+                        real = solver.device_bytes
+                        used += real - nb
+                        nb = real
+                        for i, r in enumerate(reqs):
+                            r.cells = solver.member_cells[i]
+                    else:
+                        reqs[0].cells = solver.n_cells
+                        with dev_lock:
+                            if gkey in dev:
+                                dev.move_to_end(gkey)
+                    active.append(_Slot(solver, reqs, reqs[0].steps, nb, gkey))
+                    self.peak_used = max(self.peak_used, used)
+                    self.peak_active = max(self.peak_active, len(active) + len(creating))
+                    busy = True
+                # queue the next chunk of every idle solve
+                for sl in active:
+                    if sl.remaining > 0 and sl.solver.query():
+                        k = min(self.chunk, sl.remaining)
+                        sl.solver.step(k)
+                        sl.remaining -= k
+                        busy = True
+                # collect finished solves
+                for sl in list(active):
+                    if sl.remaining == 0 and sl.solver.query():
+                        tnow = time.perf_counter() - t0
+                        for i, r in enumerate(sl.reqs):
+                            r.result, r.t, r.steps_done = sl.solver.member_read(i)
+                            r.finished = tnow
+                        sl.solver.close()
+                        used -= sl.bytes
+                        if sl.key is not None:
+                            inuse[sl.key] -= 1
+                        active.remove(sl)
+                        busy = True
+                if not busy:
+                    time.sleep(0.0002)
+        finally:
+            worker.shutdown(wait=True)
+            with dev_lock:
+                for dm in dev.values():
+                    dm.release()
+                dev.clear()
         return requests
 
 

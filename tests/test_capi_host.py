@@ -93,3 +93,12 @@ def test_init_rejects_bad_parameters_before_touching_the_device():
             H.Solver(m, q, **kw)
         assert e.value.code == H.HGKS_EINVAL
     assert m.n_cells == len(cells)  # the caller still owns the mesh
+
+
+def test_device_byte_accounting_splits_into_mesh_and_solver_parts():
+    xyz, cells, per = I.kuhn_cube(5, jitter=0.1, seed=2)
+    m = H.Mesh(xyz, cells, per)
+    assert m.info(5) == m.info(7) + m.info(8)
+    assert m.info(6) == m.info(7) + m.info(9)
+    # binary32 work arrays are smaller than binary64 ones; the mesh arrays are shared
+    assert 0 < m.info(9) < m.info(8) < m.info(7)
