@@ -33,13 +33,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # Executed binary64 operations per face of the FP64 flux kernel
-# k_flux_gp<double, 3, inviscid> (sass dadd + dmul + 2 dfma per launch,
-# divided by the faces of the launch, ncu on the 12^3 x 6 mesh), and its DRAM
-# bytes per face (dram__bytes_read + dram__bytes_write of one launch on the
+# k_flux<double, 3, inviscid> (sass dadd + dmul + 2 dfma per launch, divided
+# by the faces of the launch, ncu on the 12^3 x 6 mesh), and its DRAM bytes
+# per face (dram__bytes_read + dram__bytes_write of one launch on the
 # 40^3 x 6 mesh, 768,000 faces, larger than L2; the traffic grows with the
 # faces).  Set to None when the kernel changes until measured again.
-FP64_FLOPS_PER_FACE_INVISCID = 5037  # 104.45 Mflop per launch / 20736 faces
-FP64_FLUX_DRAM_BYTES_PER_FACE = 497.07  # (330.75 + 51.01) MB / 768000 faces
+FP64_FLOPS_PER_FACE_INVISCID = 5038  # 104.47 Mflop per launch / 20736 faces
+FP64_FLUX_DRAM_BYTES_PER_FACE = 469.0  # (312.29 + 47.90) MB / 768000 faces
 # Algorithmic bytes per cell of one binary32 reconstruction launch (k_recon_rs)
 # on tetrahedra: binary64 pseudo-inverse rows (9K + 3 M KM) x 8 B, sub-stencil
 # positions M KM, stencil indices 4K, second moments and 1/h 7 x 8 B, the
@@ -365,7 +365,7 @@ def main():
     prof = solver.profile(K)
     flux_ms = prof[2] / 2.0  # two flux launches per step
     nf = H.Mesh(w["xyz"], w["cells"], w["periods"], w.get("bfn"), w.get("bft")).n_faces
-    roof = {"bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS, "kernel": "k_flux_gp (FP64)",
+    roof = {"bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS, "kernel": "k_flux (FP64)",
             "peak_source": "derived: 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz (measured FMA chain: 1.125 TFLOP/s)",
             "achieved": None, "frac": None, "traffic": None,
             "kernel_ms_per_step": {"finalize": prof[0], "ghost+recon": prof[1], "flux": prof[2], "update": prof[3]}}

@@ -1370,12 +1370,14 @@ __global__ void __launch_bounds__(kBlock, MINB) k_flux_gp(DevMesh m, DevParams P
   }
 }
 
-// Gather of the face fluxes into L and dL/dt of cell c (Eq. finite).  The
-// face sum runs in the flux precision; L and dL enter the S2O4 sums in binary64.
+// Gather of the face fluxes of cell c (Eq. finite): the signed face sums a
+// (of F) and b (of dF/dt), with L = -a/|cell| and dL/dt = -b/|cell|.  The
+// face sum runs in the flux precision; the sums enter the S2O4 update in
+// binary64, where the factor -1/|cell| is folded into the stage coefficients.
 template <typename Real, int NFC>
-__device__ __forceinline__ void gather(const DevMesh& m, const Real* __restrict__ Fs, int64_t c, double L[5],
-                                       double dL[5]) {
-  Real a[5] = {0, 0, 0, 0, 0}, b[5] = {0, 0, 0, 0, 0};
+__device__ __forceinline__ void gather(const DevMesh& m, const Real* __restrict__ Fs, int64_t c, double a[5],
+                                       double b[5]) {
+  Real sa[5] = {0, 0, 0, 0, 0}, sb[5] = {0, 0, 0, 0, 0};
 #pragma unroll
   for (int p = 0; p < NFC; ++p) {
     const int32_t e = m.cface[p * m.nc + c];
@@ -1384,19 +1386,18 @@ __device__ __forceinline__ void gather(const DevMesh& m, const Real* __restrict_
     load_flux(Fs, f, x);
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      a[v] += (e & 1) ? -x[v] : x[v];
-      b[v] += (e & 1) ? -x[5 + v] : x[5 + v];
+      sa[v] += (e & 1) ? -x[v] : x[v];
+      sb[v] += (e & 1) ? -x[5 + v] : x[5 + v];
     }
   }
-  const double vi = -m.volinv[c];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     if constexpr (sizeof(Real) == 4) {
-      L[v] = f2d(a[v]) * vi;
-      dL[v] = f2d(b[v]) * vi;
+      a[v] = f2d(sa[v]);
+      b[v] = f2d(sb[v]);
     } else {
-      L[v] = a[v] * vi;
-      dL[v] = b[v] * vi;
+      a[v] = sa[v];
+      b[v] = sb[v];
     }
   }
 }
@@ -1410,15 +1411,17 @@ __global__ void __launch_bounds__(kBlock) k_update1(DevMesh m, const Real* __res
   if (c >= m.nc) return;
   const double dt = ctl[member_of(m, c)].dt;
   if (dt == 0.0) return;
-  double L[5], dL[5];
-  gather<Real, NFC>(m, Fs, c, L, dL);
+  double a[5], b[5];
+  gather<Real, NFC>(m, Fs, c, a, b);
+  const double r1 = -dt * m.volinv[c], r2 = r1 * dt;  // dt L = r1 a, dt^2 dL = r2 b
+  const double h1 = 0.5 * r1, h2 = 0.125 * r2, k2 = r2 * (1.0 / 6.0);
   double qs[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     const double q = Q[v * m.nce + c];
-    qs[v] = q + 0.5 * dt * L[v] + 0.125 * dt * dt * dL[v];
+    qs[v] = fma(h2, b[v], fma(h1, a[v], q));
     Qs[v * m.nce + c] = qs[v];
-    R[v * m.nc + c] = q + dt * L[v] + dt * dt / 6.0 * dL[v];
+    R[v * m.nc + c] = fma(k2, b[v], fma(r1, a[v], q));
   }
   if (Qf) store_qf(Qf, c, qs);
 }
@@ -1434,13 +1437,14 @@ __global__ void __launch_bounds__(kBlock) k_update2(DevMesh m, DevParams P, cons
   const int mid = c < m.nc ? member_of(m, c) : -1;
   const double dt = mid >= 0 ? ctl[mid].dt : 0.0;
   if (dt != 0.0) {
-    double L[5], dL[5];
-    gather<Real, NFC>(m, Fs, c, L, dL);
+    double a[5], b[5];
+    gather<Real, NFC>(m, Fs, c, a, b);
+    const double k2 = -dt * dt * m.volinv[c] * (1.0 / 3.0);  // dt^2/3 dL = k2 b
     double q[5];
     bool finite = true;
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      q[v] = R[v * m.nc + c] + dt * dt / 3.0 * dL[v];
+      q[v] = fma(k2, b[v], R[v * m.nc + c]);
       finite = finite && isfinite(q[v]);
       Q[v * m.nce + c] = q[v];
     }
@@ -1479,7 +1483,8 @@ __global__ void k_operator(DevMesh m, const Real* __restrict__ Fs, double* __res
   if (c >= m.nc) return;
   double a[5], b[5];
   gather<Real, NFC>(m, Fs, c, a, b);
-  for (int v = 0; v < 5; ++v) { L[v * m.nc + c] = a[v]; dL[v * m.nc + c] = b[v]; }
+  const double vi = -m.volinv[c];
+  for (int v = 0; v < 5; ++v) { L[v * m.nc + c] = a[v] * vi; dL[v * m.nc + c] = b[v] * vi; }
 }
 
 inline unsigned blocks(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
