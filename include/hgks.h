@@ -95,8 +95,10 @@ typedef struct {
  *                  the same operations in the same order and agree to a few
  *                  units in the last place (the compiler may fuse a
  *                  multiply and an add in one variant and not in another);
- *                  each variant is deterministic.  0: the defaults, flux per
- *                  face, rows staged.
+ *                  each variant is deterministic.  0: the defaults, rows
+ *                  staged, and flux per Gauss point for meshes with fewer
+ *                  than 16 (FP64) or 2 (FP32_MIXED) x 128 faces per SM, per
+ *                  face above.
  *   stream         cudaStream_t to run on, or NULL for a library stream. */
 typedef struct {
   double gamma, mu_ref, T_ref, visc_exp, Pr, cfl, tau_num_c, weno_eps, weno_gamma_lin;

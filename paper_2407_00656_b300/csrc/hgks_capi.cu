@@ -435,7 +435,16 @@ int make_solver(hgks_dmesh* d, const hgks_params* params, const double* const* q
   for (int i = 0; i < 5; ++i) dp.qinf[i] = params->q_inf[i];
   dp.viscous = (params->mu_ref > 0.0 || params->tau_num_c > 0.0) ? 1 : 0;
   hgks::fill_float_params(dp);
-  dp.flux_variant = 0;
+  // default flux variant by size: one thread per Gauss point while one
+  // thread per face would leave the SMs short of threads (a per-face thread
+  // is a long dependent chain), measured crossovers: binary64 at about 16
+  // blocks of 128 per SM, binary32 at about 2
+  {
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t per_sm = f32 ? 2 : 16;
+    dp.flux_variant = dm.nf < per_sm * sms * 128 ? 1 : 0;
+  }
   dp.recon_variant = 0;
   hgks::prepare_kernels(dm, s->precision);
   // initial states (the ghost slots and Q* start at zero)

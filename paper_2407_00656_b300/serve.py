@@ -116,7 +116,11 @@ class _Slot:
 class Server:
     def __init__(self, mem_budget: int, precision: int = H.HGKS_FP32_MIXED, chunk_steps: int = 10,
                  small_cells: int = 60_000, max_batch: int = 16, batch_cells: int = 300_000,
-                 cache: MeshCache | None = None):
+                 cache: MeshCache | None = None, flux_variant: int = 0):
+        # every solver runs the same flux kernel variant (the library's
+        # default depends on the mesh size, and a batch is larger than its
+        # members): a request's result then does not depend on its company
+        self.flux_variant = flux_variant
         self.mem_budget = int(mem_budget)
         self.precision = precision
         self.chunk = chunk_steps
@@ -150,10 +154,14 @@ class Server:
                 dm = H.DeviceMesh(mesh)
                 with dev_lock:
                     dev[key] = dm
-            return H.Solver(dm, q, precision=self.precision, **params)
+            s = H.Solver(dm, q, precision=self.precision, **params)
+            s.set_tuning(self.flux_variant, 0)
+            return s
 
         def create_batch(meshes, states, params):
-            return H.Solver([m.clone() for m in meshes], states, precision=self.precision, **params)
+            s = H.Solver([m.clone() for m in meshes], states, precision=self.precision, **params)
+            s.set_tuning(self.flux_variant, 0)
+            return s
 
         def evict(need):
             """Release idle device meshes (least recently used first) until

@@ -1,8 +1,9 @@
-"""Serving loop: admission by device memory, resident solves on separate
-streams, small requests batched into one solver, chunked interleaving.
-Every request's result is the same in the mix as when solved alone: bitwise,
-since each solve runs the same kernels in the same order whichever stream or
-batch it is on (FP32-mixed, autotuning off)."""
+"""Serving loop: admission by device memory, device meshes shared per
+geometry, resident solves on separate streams, small requests batched into
+one solver, chunked interleaving.  Every request's result is the same in the
+mix as when solved alone: bitwise, since each solve runs the same kernels in
+the same order whichever stream, batch or shared device mesh it is on
+(FP32-mixed, the server's pinned flux variant)."""
 import numpy as np
 import pytest
 
@@ -21,9 +22,11 @@ def mix():
     return reqs
 
 
-def alone(cache, r):
+def alone(cache, r, flux_variant=0):
+    """The request solved by itself, with the flux variant the server pins."""
     mesh, q = cache.get(r.kind, r.size)
     s = H.Solver(mesh, q, precision=H.HGKS_FP32_MIXED, **r.params)
+    s.set_tuning(flux_variant, 0)
     s.step(r.steps)
     out = s.read()
     s.close()
@@ -33,10 +36,11 @@ def alone(cache, r):
 def test_results_in_the_mix_equal_results_alone():
     cache = S.MeshCache()
     reqs = mix()
-    server = S.Server(mem_budget=8 << 30, chunk_steps=3, small_cells=5000, cache=cache)
+    server = S.Server(mem_budget=8 << 30, chunk_steps=3, small_cells=1000, cache=cache)
     server.run(reqs, time_limit=300)
+    assert any(r.cells >= 1000 for r in reqs) and any(r.cells < 1000 for r in reqs)
     for r in reqs:
-        q, t, n = alone(cache, r)
+        q, t, n = alone(cache, r, server.flux_variant)
         assert r.steps_done == n == 20
         assert r.t == t
         assert np.array_equal(r.result, q), r.rid
