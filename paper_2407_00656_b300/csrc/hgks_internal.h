@@ -41,9 +41,10 @@ struct DevParams {
   double gamma, Kint, mu_ref, T_ref, visc_exp, Pr, cfl, tau_c, eps, glin;
   double qinf[5];
   double kq, kqi;  // (K+3)/4 and its reciprocal
+  double prfix;    // 1/Pr - 1 (Prandtl-number fix of the energy flux)
   // binary32 copies, rounded on the host, for the mixed-precision kernels
   // (keeps binary64 -> binary32 conversions off the device's FP64 pipe)
-  float f_gamma, f_Kint, f_kq, f_kqi, f_mu_ref, f_T_ref, f_visc_exp, f_Pr, f_tau_c, f_eps, f_glin;
+  float f_gamma, f_Kint, f_kq, f_kqi, f_mu_ref, f_T_ref, f_visc_exp, f_Pr, f_prfix, f_tau_c, f_eps, f_glin;
   float f_qinf[5];
   int viscous;  // 1 when mu_ref > 0 or tau_c > 0 (collision time may be non-zero)
   // kernel variants chosen by the autotuner:
@@ -55,6 +56,7 @@ struct DevParams {
 inline void fill_float_params(DevParams& p) {
   p.kq = 0.25 * (p.Kint + 3.0);
   p.kqi = 4.0 / (p.Kint + 3.0);
+  p.prfix = 1.0 / p.Pr - 1.0;
   p.f_gamma = (float)p.gamma;
   p.f_Kint = (float)p.Kint;
   p.f_kq = (float)(0.25 * (p.Kint + 3.0));
@@ -63,6 +65,7 @@ inline void fill_float_params(DevParams& p) {
   p.f_T_ref = (float)p.T_ref;
   p.f_visc_exp = (float)p.visc_exp;
   p.f_Pr = (float)p.Pr;
+  p.f_prfix = (float)p.prfix;
   p.f_tau_c = (float)p.tau_c;
   p.f_eps = (float)p.eps;
   p.f_glin = (float)p.glin;

@@ -371,7 +371,7 @@ __device__ __forceinline__ void side_terms(const Prim<R>& p, const Mom<R>& M, R 
 
 template <typename R>
 struct FluxParams {
-  R gamma, Kint, kq, kqi, mu_ref, T_ref, visc_exp, Pr, tau_c;  // kq = (K+3)/4, kqi = 1/kq
+  R gamma, Kint, kq, kqi, mu_ref, T_ref, visc_exp, prfix, tau_c;  // kq = (K+3)/4, kqi = 1/kq, prfix = 1/Pr - 1
 };
 template <typename R>
 __device__ __forceinline__ FluxParams<R> flux_params(const DevParams& P) {
@@ -383,7 +383,7 @@ __device__ __forceinline__ FluxParams<R> flux_params(const DevParams& P) {
   F.mu_ref = pick<R>(P.mu_ref, P.f_mu_ref);
   F.T_ref = pick<R>(P.T_ref, P.f_T_ref);
   F.visc_exp = pick<R>(P.visc_exp, P.f_visc_exp);
-  F.Pr = pick<R>(P.Pr, P.f_Pr);
+  F.prfix = pick<R>(P.prfix, P.f_prfix);
   F.tau_c = pick<R>(P.tau_c, P.f_tau_c);
   return F;
 }
@@ -391,9 +391,10 @@ __device__ __forceinline__ FluxParams<R> flux_params(const DevParams& P) {
 // Gas-kinetic flux in the local frame (normal = first axis).
 //   ql, qr: conservative states on the two sides of the Gauss point
 //   dl[j], dr[j]: their derivatives along the local axes j = n, t1, t2
-// Output: F^n and dF/dt of Eq. expansion-1 (Section 2.2) for step dt.
+// Output: F^n and dF/dt of Eq. expansion-1 (Section 2.2) for step dt
+// (dt2i = 2/dt).
 template <typename R, bool VISC>
-__device__ void gks_flux(const R ql[5], const R dl[3][5], const R qr[5], const R dr[3][5], R dt,
+__device__ void gks_flux(const R ql[5], const R dl[3][5], const R qr[5], const R dr[3][5], R dt, R dt2i,
                          const FluxParams<R>& P, R F[5], R dF[5]) {
   const R K = P.Kint;
   const Prim<R> pl = prim_of(ql, P.kq, P.kqi), pr = prim_of(qr, P.kq, P.kqi);
@@ -446,85 +447,91 @@ __device__ void gks_flux(const R ql[5], const R dl[3][5], const R qr[5], const R
     // (T0/T_ref)^e as exp(e log(T0/T_ref)): a few units in the last place,
     // for about half the cost of pow
     if (P.visc_exp != R(0) && mu != R(0)) mu = P.mu_ref * exp(P.visc_exp * log(p0.h2 / P.T_ref));  // T0 = 1/(2 lam0)
-    const R tau = mu / p0p + P.tau_c * dt * fabs(plp - prp) / (plp + prp);
+    const R sp = plp + prp;
+    const R tau = (mu * sp + P.tau_c * dt * fabs(plp - prp) * p0p) / (p0p * sp);  // one division
     if (!(tau > R(0))) {
 #pragma unroll
       for (int i = 0; i < 5; ++i) { F[i] = Fe[i]; dF[i] = Ye[i]; }
       return;
     }
-    // rho0 <u (abar.u) psi> on the full line of g0
-    Mom<R> M0;
-    R E0;
-    moments<5>(p0, 0, K, M0, E0);
-    R X0[5];
-    side_terms(p0, M0, E0, K, P.kqi, dq0, X0);
-    // side terms of the initial non-equilibrium distribution
-    R Xl[5], Xr[5], Nk[5], Yk[5];
-    side_terms(pl, Ml, El, K, P.kqi, dl, Xl);
-    side_terms(pr, Mr, Er, K, P.kqi, dr, Xr);
-    {
-      R tmp[5], s1[5], s2[5], Pp[5], yl[5], yr[5], nl[5], nr[5];
-      // rho_l <u A^l psi> over u > 0
-      const EState<R> sl = estate(ql, P.gamma);
-      euler_jv<0>(sl, dl[0], tmp);
-      euler_jv<1>(sl, dl[1], s1);
-      euler_jv<2>(sl, dl[2], s2);
-#pragma unroll
-      for (int i = 0; i < 5; ++i) tmp[i] = -(tmp[i] + s1[i] + s2[i]);
-      prim_pert(pl, P.kqi, tmp, Pp);
-      phi_jet<1, 0, 0>(Ml, pl, El, K, Pp, yl);
-      // rho_r <u A^r psi> over u < 0
-      const EState<R> sr = estate(qr, P.gamma);
-      euler_jv<0>(sr, dr[0], tmp);
-      euler_jv<1>(sr, dr[1], s1);
-      euler_jv<2>(sr, dr[2], s2);
-#pragma unroll
-      for (int i = 0; i < 5; ++i) tmp[i] = -(tmp[i] + s1[i] + s2[i]);
-      prim_pert(pr, P.kqi, tmp, Pp);
-      phi_jet<1, 0, 0>(Mr, pr, Er, K, Pp, yr);
-      // rho <u psi>: the derivative along P = (1, 0, 0, 0, 0) is the value
-      const R e0[5] = {R(1), R(0), R(0), R(0), R(0)};
-      phi_jet<1, 0, 0>(Ml, pl, El, K, e0, nl);
-      phi_jet<1, 0, 0>(Mr, pr, Er, K, e0, nr);
-#pragma unroll
-      for (int i = 0; i < 5; ++i) {
-        Nk[i] = pl.rho * nl[i] + pr.rho * nr[i];
-        Yk[i] = yl[i] + yr[i];
-      }
-    }
     // time-integral coefficients of the fit F = (4 I(dt/2) - I(dt))/dt,
     // dF = 4 (I(dt) - 2 I(dt/2))/dt^2, with h = dt/2, r = tau/h and
     // em = 1 - exp(-h/tau)
-    const R h = R(0.5) * dt;
-    const R r = tau / h;
-    const R em = -expm1(-h / tau);
+    const R r = tau * dt2i;  // dt2i = 1/h
+    const R em = -expm1(R(-1) / r);
     const R g = em * (R(2) + em);  // 3 - 4 e^{-h/tau} + e^{-2h/tau}
     const R C1 = R(1) - R(0.5) * r * g;
     const R C2 = tau * (r * g - (R(2) - em * em));
     const R C3 = tau * (R(0.5) * r * g - R(1));
     const R C4 = R(0.5) * r * g;
     const R C5 = tau * (r * g - (R(1) - em * em));
-    const R D1 = r * em * em / h;
+    const R D1 = r * em * em * dt2i;
     const R D2 = R(2) * r * em * (R(1) - em) - R(2) * r * r * em * em;
     const R D3 = R(1) - r * r * em * em;
     const R D4 = -D1;
     const R D5 = D2;
+    // F = C1 Fe + C2 X0 + C3 Ye + C4 Nk - C5 (Xl + Xr) - tau C4 Yk, and dF
+    // with D1..D5, accumulated term by term as each term is formed (this
+    // keeps few of them live at once)
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
-      const R xk = Xl[i] + Xr[i];
-      F[i] = C1 * Fe[i] + C2 * X0[i] + C3 * Ye[i] + C4 * Nk[i] - C5 * xk - tau * C4 * Yk[i];
-      dF[i] = D1 * Fe[i] + D2 * X0[i] + D3 * Ye[i] + D4 * Nk[i] - D5 * xk - tau * D4 * Yk[i];
+      F[i] = C1 * Fe[i] + C3 * Ye[i];
+      dF[i] = D1 * Fe[i] + D3 * Ye[i];
     }
-    // Prandtl-number fix of the energy flux: + (1/Pr - 1) q with q the heat
-    // flux of the first-order equilibrium part, -tau rho0 <c_u c^2/2 (abar.u+Abar)>,
-    // which by the compatibility condition reduces to -tau w.(X0 + Y0),
-    // w = (|U0|^2/2, -U0, -V0, -W0, 1).
-    if (P.Pr != R(1)) {
-      const R qh = -tau * (R(0.5) * (p0.U * p0.U + p0.V * p0.V + p0.W * p0.W) * (X0[0] + Ye[0]) -
-                           p0.U * (X0[1] + Ye[1]) - p0.V * (X0[2] + Ye[2]) - p0.W * (X0[3] + Ye[3]) +
-                           (X0[4] + Ye[4]));
-      F[4] += (R(1) / P.Pr - R(1)) * qh;
+    {
+      // X0 = rho0 <u (abar.u) psi> on the full line of g0
+      Mom<R> M0;
+      R E0;
+      moments<5>(p0, 0, K, M0, E0);
+      R X0[5];
+      side_terms(p0, M0, E0, K, P.kqi, dq0, X0);
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        F[i] += C2 * X0[i];
+        dF[i] += D2 * X0[i];
+      }
+      // Prandtl-number fix of the energy flux: + (1/Pr - 1) q with q the heat
+      // flux of the first-order equilibrium part, -tau rho0 <c_u c^2/2 (abar.u+Abar)>,
+      // which by the compatibility condition reduces to -tau w.(X0 + Y0),
+      // w = (|U0|^2/2, -U0, -V0, -W0, 1).
+      if (P.prfix != R(0)) {
+        const R qh = -tau * (R(0.5) * (p0.U * p0.U + p0.V * p0.V + p0.W * p0.W) * (X0[0] + Ye[0]) -
+                             p0.U * (X0[1] + Ye[1]) - p0.V * (X0[2] + Ye[2]) - p0.W * (X0[3] + Ye[3]) +
+                             (X0[4] + Ye[4]));
+        F[4] += P.prfix * qh;
+      }
     }
+    // the initial non-equilibrium distribution of each side: spatial slopes
+    // X, time slope Y = rho <u A psi> with rho <A psi> = -sum_j J_j(q) d_j,
+    // and N = rho <u psi>
+    auto side = [&](const R q[5], const R d[3][5], const Prim<R>& p, const Mom<R>& M, R Eh) {
+      R X[5];
+      side_terms(p, M, Eh, K, P.kqi, d, X);
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        F[i] -= C5 * X[i];
+        dF[i] -= D5 * X[i];
+      }
+      R tmp[5], s1[5], s2[5], Pp[5], y[5], nn[5];
+      const EState<R> st = estate(q, P.gamma);
+      euler_jv<0>(st, d[0], tmp);
+      euler_jv<1>(st, d[1], s1);
+      euler_jv<2>(st, d[2], s2);
+#pragma unroll
+      for (int i = 0; i < 5; ++i) tmp[i] = -(tmp[i] + s1[i] + s2[i]);
+      prim_pert(p, P.kqi, tmp, Pp);
+      phi_jet<1, 0, 0>(M, p, Eh, K, Pp, y);
+      // rho <u psi>: the derivative along P = (1, 0, 0, 0, 0) is the value
+      const R e0[5] = {R(1), R(0), R(0), R(0), R(0)};
+      phi_jet<1, 0, 0>(M, p, Eh, K, e0, nn);
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        F[i] += C4 * (p.rho * nn[i]) - tau * C4 * y[i];
+        dF[i] += D4 * (p.rho * nn[i]) - tau * D4 * y[i];
+      }
+    };
+    side(ql, dl, pl, Ml, El);
+    side(qr, dr, pr, Mr, Er);
   }
 }
 
@@ -1221,7 +1228,7 @@ __device__ __forceinline__ void load_flux(const double* __restrict__ Fs, int64_t
 template <typename Real, int G, bool VISC>
 __device__ __forceinline__ Real point_flux(const DevMesh& m, const DevParams& P, const FluxParams<Real>& FP,
                                            const Real* __restrict__ coef, int64_t f, int g, int64_t own, int nbr,
-                                           Real dt, Real r[10]) {
+                                           Real dt, Real dt2i, Real r[10]) {
   const int64_t nf = m.nf;
   // planar triangles share one normal; bilinear quads have one per point
   Real n[3], t1[3], t2[3];
@@ -1288,7 +1295,7 @@ __device__ __forceinline__ Real point_flux(const DevMesh& m, const DevParams& P,
       for (int v = 0; v < 5; ++v) dr[j][v] = Real(0);
   }
   Real Fl[5], Dl[5];
-  gks_flux<Real, VISC>(ql, dl, qr, dr, dt, FP, Fl, Dl);
+  gks_flux<Real, VISC>(ql, dl, qr, dr, dt, dt2i, FP, Fl, Dl);
   // back to the global frame
   r[0] = Fl[0];
   r[4] = Fl[4];
@@ -1304,8 +1311,11 @@ __device__ __forceinline__ Real point_flux(const DevMesh& m, const DevParams& P,
 
 // Face flux, one thread per face: sum over the Gauss points of weight*area
 // times the point flux.  Output: the flux record of each face (store_flux).
+// (binary32 with viscosity: capped at 168 registers, 3 blocks per SM, which
+// the term-by-term accumulation of gks_flux fits without spilling)
 template <typename Real, int G, bool VISC>
-__global__ void __launch_bounds__(kBlock) k_flux(DevMesh m, DevParams P, const Real* __restrict__ coef,
+__global__ void __launch_bounds__(kBlock, (sizeof(Real) == 4 && VISC) ? 3 : 1)
+    k_flux(DevMesh m, DevParams P, const Real* __restrict__ coef,
                                                  Real* __restrict__ Fs, const Control* __restrict__ ctl) {
   const int64_t nf = m.nf;
   const int64_t f = (int64_t)blockIdx.x * kBlock + threadIdx.x;
@@ -1313,7 +1323,7 @@ __global__ void __launch_bounds__(kBlock) k_flux(DevMesh m, DevParams P, const R
   const int64_t own = m.fown[f];
   const double dtd = ctl[member_of(m, own)].dt;
   if (dtd == 0.0) return;
-  const Real dt = cvt<Real>(dtd);
+  const Real dt = cvt<Real>(dtd), dt2i = Real(2) / dt;
   const FluxParams<Real> FP = flux_params<Real>(P);
   const int nbr = m.fnbr[f];
   Real acc[10];
@@ -1322,7 +1332,7 @@ __global__ void __launch_bounds__(kBlock) k_flux(DevMesh m, DevParams P, const R
 #pragma unroll 1
   for (int g = 0; g < G; ++g) {
     Real r[10];
-    const Real w = point_flux<Real, G, VISC>(m, P, FP, coef, f, g, own, nbr, dt, r);
+    const Real w = point_flux<Real, G, VISC>(m, P, FP, coef, f, g, own, nbr, dt, dt2i, r);
 #pragma unroll
     for (int v = 0; v < 10; ++v) acc[v] = fma(w, r[v], acc[v]);
   }
@@ -1350,7 +1360,8 @@ __global__ void __launch_bounds__(kBlock, MINB) k_flux_gp(DevMesh m, DevParams P
 #pragma unroll
     for (int v = 0; v < 10; ++v) r[v] = Real(0);
     if (dtd != 0.0)
-      w = point_flux<Real, G, VISC>(m, P, flux_params<Real>(P), coef, f, gp, own, m.fnbr[f], cvt<Real>(dtd), r);
+      w = point_flux<Real, G, VISC>(m, P, flux_params<Real>(P), coef, f, gp, own, m.fnbr[f], cvt<Real>(dtd),
+                                    Real(2) / cvt<Real>(dtd), r);
     sw[gp][fl] = w;
 #pragma unroll
     for (int v = 0; v < 10; ++v) sr[gp][v][fl] = r[v];
