@@ -1311,10 +1311,10 @@ __device__ __forceinline__ Real point_flux(const DevMesh& m, const DevParams& P,
 
 // Face flux, one thread per face: sum over the Gauss points of weight*area
 // times the point flux.  Output: the flux record of each face (store_flux).
-// (binary32 with viscosity: capped at 168 registers, 3 blocks per SM, which
-// the term-by-term accumulation of gks_flux fits without spilling)
+// (binary32 register caps that fit without spilling, measured fastest:
+// inviscid 96 registers, 5 blocks per SM; with viscosity 168, 3 blocks per SM)
 template <typename Real, int G, bool VISC>
-__global__ void __launch_bounds__(kBlock, (sizeof(Real) == 4 && VISC) ? 3 : 1)
+__global__ void __launch_bounds__(kBlock, sizeof(Real) == 4 ? (VISC ? 3 : 5) : 1)
     k_flux(DevMesh m, DevParams P, const Real* __restrict__ coef,
                                                  Real* __restrict__ Fs, const Control* __restrict__ ctl) {
   const int64_t nf = m.nf;
