@@ -135,6 +135,25 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest of x over the ranks: a job's time is its slowest rank's.
+    dist is torch.distributed (or None for one process); device holds the
+    reduction tensor ("cuda" for NCCL, "cpu" for gloo)."""
+    if dist is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(cells: int, steps: int, world: int, seconds: float) -> float:
+    """Whole-job cell-updates/s of `world` replicas that each advance `cells`
+    cells by `steps` steps, timed by the slowest replica."""
+    return cells * steps * world / seconds
+
+
 def cpu_baseline(w, budget_steps: int = 3):
     """The CPU checker as it stands, all host cores, on one step of the same mesh."""
     import oracle
@@ -353,12 +372,8 @@ def main():
         e1.synchronize()
     torch.cuda.synchronize()
     barrier()
-    ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = nc * K * world / (ms * 1e-3)
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+    value = replica_throughput(nc, K, world, ms * 1e-3)
 
     # ---- per-kernel-group times (separate profiled pass of K steps, events
     # around each group on the solver's stream)
@@ -390,8 +405,8 @@ def main():
         solver.write(qh, 0.0)
         solver.step(1)
         solver.read(out)
-    t_e2e = time.perf_counter() - t0
-    e2e = {"value": nc * e2e_steps * world / t_e2e, "unit": "cell-updates/s",
+    t_e2e = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    e2e = {"value": replica_throughput(nc, e2e_steps, world, t_e2e), "unit": "cell-updates/s",
            "h2d_bytes_per_step": int(qh.nbytes), "d2h_bytes_per_step": int(out.nbytes)}
 
     extra = {}
