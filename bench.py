@@ -310,6 +310,7 @@ def main():
     ap.add_argument("--error-steps", type=int, default=None,
                     help="steps of the mixed-vs-FP64 comparison (default: the --steps value)")
     ap.add_argument("--serve", action="store_true", help="run the full serving stream (256 requests, up to 2M cells)")
+    ap.add_argument("--no-graph", action="store_true", help="launch each step's kernels one by one (no CUDA graph)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -353,7 +354,8 @@ def main():
     nc = len(w["cells"])
     stream = torch.cuda.Stream()
     mesh = H.Mesh(w["xyz"], w["cells"], w["periods"], w.get("bfn"), w.get("bft"))
-    solver = H.Solver(mesh, w["q"], precision=prec, stream=stream.cuda_stream, **w["params"])
+    solver = H.Solver(mesh, w["q"], precision=prec, stream=stream.cuda_stream, use_graph=0 if args.no_graph else 1,
+                      **w["params"])
     W, K = max(args.warmup, 3), args.steps
     solver.step(W)
     solver.sync()
@@ -420,6 +422,7 @@ def main():
                 "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64" if prec == H.HGKS_FP64 else "f32-mixed", "data": "synthetic",
                 "config": {"workload": w["desc"], "cells": nc, "faces": nf, "precision": args.precision,
+                           "cuda_graph": not args.no_graph,
                            "l2": "inputs larger than L2 (pseudo-inverses alone exceed 126 MB)",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roof, "e2e": e2e, "gpu_launches": K * launches_per_step + 1,

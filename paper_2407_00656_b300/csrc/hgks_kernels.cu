@@ -157,17 +157,22 @@ struct Prim {
 };
 
 // kq = (K+3)/4: rho E = rho |U|^2/2 + kq rho / lam, so lam = kq rho / eint and
-// 1/(2 lam) = eint / (2 kq rho); two reciprocals per state.
+// 1/(2 lam) = eint / (2 kq rho), with eint = rho E - |rho U|^2/(2 rho).  Both
+// reciprocals, 1/rho and 1/eint, come from one division: with
+// e2 = rho eint = rho (rho E) - |rho U|^2/2, d = 1/(rho e2) gives
+// 1/rho = e2 d and 1/eint = rho^2 d.
 template <typename R>
 __device__ __forceinline__ Prim<R> prim_of(const R q[5], R kq, R kqi) {
   Prim<R> p;
   p.rho = q[0];
-  const R ri = R(1) / q[0];
+  const R e2 = q[0] * q[4] - R(0.5) * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  const R d = R(1) / (q[0] * e2);
+  const R ri = e2 * d;
   p.U = q[1] * ri;
   p.V = q[2] * ri;
   p.W = q[3] * ri;
-  const R eint = q[4] - R(0.5) * (q[1] * p.U + q[2] * p.V + q[3] * p.W);
-  p.lam = kq * q[0] / eint;
+  const R eint = e2 * ri;
+  p.lam = kq * q[0] * (q[0] * q[0] * d);
   p.h2 = R(0.5) * kqi * eint * ri;
   return p;
 }
