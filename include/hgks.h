@@ -99,6 +99,14 @@ typedef struct {
  *                  staged, and flux per Gauss point for meshes with fewer
  *                  than 16 (FP64) or 2 (FP32_MIXED) x 128 faces per SM, per
  *                  face above.
+ *   persistent     1: hgks_step runs its n steps as one persistent
+ *                  cooperative launch (every phase of every step in one
+ *                  kernel, grid-wide barriers between phases) instead of n
+ *                  graph launches; for small meshes and batches of them,
+ *                  where a step is a few short kernels.  Results agree with
+ *                  the separate kernels to a few units in the last place.
+ *                  A grid barrier that waits more than about a second ends
+ *                  the launch with HGKS_ETIMEOUT at the next sync or read.
  *   stream         cudaStream_t to run on, or NULL for a library stream. */
 typedef struct {
   double gamma, mu_ref, T_ref, visc_exp, Pr, cfl, tau_num_c, weno_eps, weno_gamma_lin;
@@ -106,7 +114,7 @@ typedef struct {
   int32_t precision;
   int32_t use_graph;
   int32_t autotune;
-  int32_t reserved;
+  int32_t persistent;
   void* stream;
 } hgks_params;
 

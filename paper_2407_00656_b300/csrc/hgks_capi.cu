@@ -48,6 +48,7 @@ struct hgks_solver {
   hgks::DevWork dw{};
   int precision = 0;
   int use_graph = 1;
+  int persistent = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   void* arena = nullptr;  // state and work arrays, stream-ordered on `stream`
@@ -107,6 +108,7 @@ int check_params(const hgks_params* p) {
   if (!(p->weno_eps > 0.0)) return fail(HGKS_EINVAL, "weno_eps must be positive");
   if (!(p->weno_gamma_lin > 0.0 && p->weno_gamma_lin < 0.125)) return fail(HGKS_EINVAL, "weno_gamma_lin must lie in (0, 1/8)");
   if (p->precision != HGKS_FP64 && p->precision != HGKS_FP32_MIXED) return fail(HGKS_EINVAL, "unknown precision");
+  if (p->persistent != 0 && p->persistent != 1) return fail(HGKS_EINVAL, "persistent must be 0 or 1");
   return HGKS_OK;
 }
 
@@ -402,6 +404,7 @@ int make_solver(hgks_dmesh* d, const hgks_params* params, const double* const* q
   const hgks::HostMesh& m = d->sizes;
   s->precision = params->precision;
   s->use_graph = params->use_graph;
+  s->persistent = params->persistent;
   const size_t bytes = (size_t)hgks::solver_work_bytes(m, s->precision, n);
   int rc = alloc_on(&s->arena, bytes, s->stream, "the solver state");
   if (rc) return bail(rc);
@@ -419,6 +422,7 @@ int make_solver(hgks_dmesh* d, const hgks_params* params, const double* const* q
   w.coef = cv.take<char>(rs * (f32 ? hgks::kCoefRec32 : hgks::kCoefRec64) * m.nc);
   w.Fs = cv.take<char>(rs * (f32 ? hgks::kFluxRec32 : hgks::kFluxRec64) * m.nf);
   w.ctl = cv.take<hgks::Control>(n);
+  w.bar = cv.take<hgks::GridBar>(1);
   if (cv.off > bytes) { g_err = "internal error: solver arena too small"; return bail(HGKS_ENOMEM); }
   // parameters
   hgks::DevParams& dp = s->dp;
@@ -608,7 +612,10 @@ int hgks_step(hgks_solver* s, int n_steps, double t_end, double dt_fixed) {
   if (n_steps < 0) return fail(HGKS_EINVAL, "n_steps must be >= 0");
   if (n_steps == 0) return HGKS_OK;
   hgks::launch_control(s->dm, s->dw, t_end, dt_fixed, s->stream);
-  if (s->use_graph) {
+  if (s->persistent) {
+    HGKS_CUDA(hgks::launch_persistent(s->dm, s->dp, s->dw, s->precision, n_steps, s->stream),
+              "launching the persistent steps");
+  } else if (s->use_graph) {
     if (!s->graph) {
       cudaGraph_t g = nullptr;
       HGKS_CUDA(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal), "beginning graph capture");

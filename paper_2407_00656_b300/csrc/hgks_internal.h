@@ -93,6 +93,12 @@ struct Control {
 
 enum { FLAG_NONFINITE = 1, FLAG_TIMEOUT = 2 };
 
+// Grid-wide barrier state of a persistent launch (zeroed before each launch).
+struct GridBar {
+  unsigned int count;  // blocks arrived at the current barrier
+  unsigned int gen;    // barriers completed
+};
+
 // Work arrays of one solver.
 struct DevWork {
   double* Q;      // [5][nce] state Q^n, ghost slots at [nc, nce)
@@ -104,6 +110,7 @@ struct DevWork {
                   // record of cell c: [v][j], j = 0: q, 1-3: g, 4-9: k
   void* Fs;       // [nf][kFluxRec] face flux sums: F (5) then dF/dt (5) (double or float)
   Control* ctl;   // [nmesh] one control block per member mesh
+  GridBar* bar;   // barrier of the persistent step kernel
 };
 
 // Message returned by hgks_last_error() on this thread.
@@ -128,6 +135,10 @@ struct StepEvents {
 // Launch one S2O4 step (Algorithm 2) on stream s; precision 0 = FP64, 1 = mixed.
 void launch_step(const DevMesh& m, const DevParams& p, const DevWork& w, int precision, cudaStream_t s,
                  const StepEvents* ev = nullptr);
+// Launch n S2O4 steps as one persistent cooperative kernel; returns the CUDA
+// error of the launch (cudaErrorCooperativeLaunchTooLarge and the like).
+cudaError_t launch_persistent(const DevMesh& m, const DevParams& p, const DevWork& w, int precision, int n,
+                              cudaStream_t s);
 // Set t_end and dt_fixed of every member for the following steps.
 void launch_control(const DevMesh& m, const DevWork& w, double t_end, double dt_fixed, cudaStream_t s);
 // Reset time/steps/flags of member `only` (every member when only < 0), copy

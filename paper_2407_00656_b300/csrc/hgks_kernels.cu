@@ -15,6 +15,7 @@
 // flux in binary32; geometry, pseudo-inverses and S2O4 sums in binary64).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cfloat>
 #include <cstdint>
 #include <type_traits>
@@ -32,6 +33,20 @@ __device__ __forceinline__ void sfor(F&& f) {
     f(std::integral_constant<int, I>{});
     sfor<N, I + 1>(f);
   }
+}
+
+// Loads of data that a kernel only reads.  COH = true: the data is written
+// by other blocks of the same (persistent) launch, so the load goes to L2
+// (ld.global.cg) instead of through the non-coherent read-only or L1 caches.
+template <bool COH, typename T>
+__device__ __forceinline__ T ldro(const T* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return __ldg(p);
+}
+template <bool COH, typename T>
+__device__ __forceinline__ T ldm(const T* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return *p;
 }
 
 // binary64 -> Real.  For binary32 the conversion is done with integer
@@ -81,10 +96,14 @@ __device__ __forceinline__ void store_qf(float* __restrict__ Qf, int64_t c, cons
   store_qf(Qf, c, q, qf);
 }
 // Variable v of cell c of a state: binary64 [5][nce] or binary32 [nce][8].
+template <bool COH = false>
 __device__ __forceinline__ double qget(const double* __restrict__ Q, int64_t nce, int v, int64_t c) {
-  return Q[v * nce + c];
+  return ldm<COH>(Q + v * nce + c);
 }
-__device__ __forceinline__ float qget(const float* __restrict__ Q, int64_t, int v, int64_t c) { return Q[8 * c + v]; }
+template <bool COH = false>
+__device__ __forceinline__ float qget(const float* __restrict__ Q, int64_t, int v, int64_t c) {
+  return ldm<COH>(Q + 8 * c + v);
+}
 
 // Records of the reconstruction coefficients and face fluxes (see DevWork).
 template <typename Real>
@@ -94,18 +113,20 @@ __host__ __device__ constexpr int flux_rec() { return sizeof(Real) == 4 ? kFluxR
 
 // Ten consecutive reals at p (8-byte aligned for binary32, 16-byte for
 // binary64), as five vector accesses.
+template <bool COH = false>
 __device__ __forceinline__ void load10(const float* __restrict__ p, float x[10]) {
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
-    const float2 t = __ldg(reinterpret_cast<const float2*>(p) + i);
+    const float2 t = ldro<COH>(reinterpret_cast<const float2*>(p) + i);
     x[2 * i] = t.x;
     x[2 * i + 1] = t.y;
   }
 }
+template <bool COH = false>
 __device__ __forceinline__ void load10(const double* __restrict__ p, double x[10]) {
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
-    const double2 t = __ldg(reinterpret_cast<const double2*>(p) + i);
+    const double2 t = ldro<COH>(reinterpret_cast<const double2*>(p) + i);
     x[2 * i] = t.x;
     x[2 * i + 1] = t.y;
   }
@@ -627,20 +648,27 @@ __global__ void k_reset(Control* ctl, int n, int only, double t) {
   c->dtmin_bits = dbits(__longlong_as_double(0x7ff0000000000000LL));
 }
 
-__global__ void k_finalize(Control* ctl, int n, double cfl) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  Control* c = ctl + i;
-  double dt = c->dt_fixed > 0.0 ? c->dt_fixed : cfl * __longlong_as_double((long long)c->dtmin_bits);
-  if (c->t_end > 0.0) dt = fmin(dt, c->t_end - c->t);
+// The step size of member c: the CFL step (or dt_fixed), clipped to t_end.
+template <bool COH = false>
+__device__ __forceinline__ void finalize_one(Control* c, double cfl) {
+  const double dt_fixed = ldm<COH>(&c->dt_fixed), t_end = ldm<COH>(&c->t_end), t = ldm<COH>(&c->t);
+  double dt = dt_fixed > 0.0 ? dt_fixed : cfl * __longlong_as_double((long long)ldm<COH>(&c->dtmin_bits));
+  if (t_end > 0.0) dt = fmin(dt, t_end - t);
   if (!(dt > 0.0) || !(dt < 1e300)) dt = 0.0;
   c->dt = dt;
   if (dt > 0.0) {
-    c->t += dt;
-    c->steps += 1;
+    c->t = t + dt;
+    c->steps = ldm<COH>(&c->steps) + 1;
     c->dtmin_bits = dbits(__longlong_as_double(0x7ff0000000000000LL));
   }
 }
+
+__global__ void k_finalize(Control* ctl, int n, double cfl) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  finalize_one(ctl + i, cfl);
+}
+
 
 // Local step bound of cell c (without the CFL factor).
 __device__ __forceinline__ double cell_dt(const double q[5], double hdt, const DevParams& P) {
@@ -674,13 +702,15 @@ __device__ __forceinline__ float cell_dt_f(const float q[5], float hdt, const De
   return dt;
 }
 
+// Minimum over a block of NW warps into *dst (every thread calls it).
+template <int NW = kBlock / 32>
 __device__ __forceinline__ void block_min_to(unsigned long long* dst, double v) {
-  __shared__ double red[kBlock / 32];
+  __shared__ double red[NW];
   for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
   if (threadIdx.x < 32) {
-    double x = threadIdx.x < kBlock / 32 ? red[threadIdx.x] : __longlong_as_double(0x7ff0000000000000LL);
+    double x = threadIdx.x < NW ? red[threadIdx.x] : __longlong_as_double(0x7ff0000000000000LL);
     for (int o = 16; o > 0; o >>= 1) x = fmin(x, __shfl_xor_sync(0xffffffffu, x, o));
     if (threadIdx.x == 0 && x >= 0.0) atomicMin(dst, dbits(x));
   }
@@ -691,9 +721,10 @@ __device__ __forceinline__ void block_min_to(unsigned long long* dst, double v) 
 // One mesh: a block reduction; a batch: a warp reduction segmented by member
 // (the minimum of positive doubles is the minimum of their bit patterns,
 // reduced as the high word, then the low word among the lanes that hold it).
+template <int NW = kBlock / 32>
 __device__ __forceinline__ void member_min_to(const DevMesh& m, Control* ctl, int mid, double v) {
   if (m.nmesh == 1) {
-    block_min_to(&ctl[0].dtmin_bits, v);
+    block_min_to<NW>(&ctl[0].dtmin_bits, v);
     return;
   }
   const unsigned long long b = dbits(v);
@@ -734,14 +765,13 @@ __global__ void __launch_bounds__(kBlock) k_dt(DevMesh m, DevParams P, const dou
 }
 
 // Ghost cell averages: the boundary map of the mirrored interior cell.
-__global__ void __launch_bounds__(kBlock) k_ghost(DevMesh m, DevParams P, double* __restrict__ Q, float* __restrict__ Qf,
-                                                  const Control* __restrict__ ctl) {
-  const int64_t g = (int64_t)blockIdx.x * kBlock + threadIdx.x;
-  if (g >= m.ng) return;
+template <bool COH = false>
+__device__ __forceinline__ void ghost_one(const DevMesh& m, const DevParams& P, double* __restrict__ Q,
+                                          float* __restrict__ Qf, const Control* __restrict__ ctl, int64_t g) {
   const int64_t s = m.gsrc[g];
-  if (ctl[member_of(m, s)].dt == 0.0) return;
+  if (ldm<COH>(&ctl[member_of(m, s)].dt) == 0.0) return;
   double q[5], o[5];
-  for (int k = 0; k < 5; ++k) q[k] = Q[k * m.nce + s];
+  for (int k = 0; k < 5; ++k) q[k] = ldm<COH>(Q + k * m.nce + s);
   if (m.gtag[g] == 3) {  // wall: momentum reversed
     o[0] = q[0]; o[1] = -q[1]; o[2] = -q[2]; o[3] = -q[3]; o[4] = q[4];
   } else {
@@ -750,6 +780,12 @@ __global__ void __launch_bounds__(kBlock) k_ghost(DevMesh m, DevParams P, double
   }
   for (int k = 0; k < 5; ++k) Q[k * m.nce + m.nc + g] = o[k];
   if (Qf) store_qf(Qf, m.nc + g, o);
+}
+
+__global__ void __launch_bounds__(kBlock) k_ghost(DevMesh m, DevParams P, double* __restrict__ Q, float* __restrict__ Qf,
+                                                  const Control* __restrict__ ctl) {
+  const int64_t g = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (g < m.ng) ghost_one(m, P, Q, Qf, ctl, g);
 }
 
 // The combined polynomial of a cell and variable is
@@ -921,21 +957,19 @@ struct ReconSmem {
   static constexpr size_t bytes = tile + sub + dq;
 };
 
-template <typename Real, typename QT, int K, int M, int KM, bool STAGE>
-__global__ void __launch_bounds__(kRThreads) k_recon(DevMesh m, DevParams P, const QT* __restrict__ Q,
-                                                     Real* __restrict__ coef, Control* __restrict__ ctl) {
+template <typename Real, typename QT, int K, int M, int KM, bool STAGE, bool COH = false>
+__device__ __forceinline__ void recon_block(const DevMesh& m, const DevParams& P, const QT* __restrict__ Q,
+                                            Real* __restrict__ coef, Control* __restrict__ ctl, int64_t c0,
+                                            unsigned char* smem_raw) {
   using S = ReconSmem<Real, K, M, KM>;
   constexpr int kRows = S::kRows;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
   // staged variant: [tile | ssub | sdq]; direct variant: [sdq] only
   double* tile = reinterpret_cast<double*>(smem_raw);                // [kRows][kRC]
   uint8_t* ssub = smem_raw + S::tile;                                // [M*KM][kRC]
   Real* sdq = reinterpret_cast<Real*>(STAGE ? smem_raw + S::tile + S::sub : smem_raw);  // [5][K][kRC]
   __shared__ __align__(8) uint64_t bar;
-  if (m.nmesh == 1 && ctl->dt == 0.0) return;  // uniform over the grid (a batch computes every member)
   const int64_t nc = m.nc, ncp = m.ncp;
   const int lane = threadIdx.x & 31, v = threadIdx.x >> 5;
-  const int64_t c0 = (int64_t)blockIdx.x * kRC;
   const int64_t c = c0 + lane;
   const bool valid = c < nc;
   if constexpr (STAGE) {
@@ -954,11 +988,11 @@ __global__ void __launch_bounds__(kRThreads) k_recon(DevMesh m, DevParams P, con
   // this warp's variable: stencil differences (overlaps the staging)
   Real qv = Real(0);
   if (valid) {
-    qv = (Real)qget(Q, m.nce, v, c);
+    qv = (Real)qget<COH>(Q, m.nce, v, c);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int64_t j = m.sten[(int64_t)k * nc + c];
-      sdq[(v * K + k) * kRC + lane] = (Real)qget(Q, m.nce, v, j) - qv;
+      sdq[(v * K + k) * kRC + lane] = (Real)qget<COH>(Q, m.nce, v, j) - qv;
     }
   }
   if constexpr (STAGE) {
@@ -1028,6 +1062,14 @@ __global__ void __launch_bounds__(kRThreads) k_recon(DevMesh m, DevParams P, con
   write_block_records<Real>(reinterpret_cast<Real*>(smem_raw), res, valid, lane, v, nv, coef, c0);
 }
 
+template <typename Real, typename QT, int K, int M, int KM, bool STAGE>
+__global__ void __launch_bounds__(kRThreads) k_recon(DevMesh m, DevParams P, const QT* __restrict__ Q,
+                                                     Real* __restrict__ coef, Control* __restrict__ ctl) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  if (m.nmesh == 1 && ctl->dt == 0.0) return;  // uniform over the grid (a batch computes every member)
+  recon_block<Real, QT, K, M, KM, STAGE>(m, P, Q, coef, ctl, (int64_t)blockIdx.x * kRC, smem_raw);
+}
+
 // WENO reconstruction in binary32 (mixed precision), one block per kRC = 32
 // cells with one warp per conservative variable, as k_recon, but with every
 // input of the block staged in shared memory by all 160 threads before any
@@ -1054,20 +1096,17 @@ struct ReconSmemF {
   static constexpr size_t bytes = tile + nbr + own + geo + sub;
 };
 
-template <int K, int M, int KM>
-__global__ void __launch_bounds__(kRThreads) k_recon_rs(DevMesh m, DevParams P, const float* __restrict__ Qf,
-                                                        float* __restrict__ coef, Control* __restrict__ ctl) {
+template <int K, int M, int KM, bool COH = false>
+__device__ __forceinline__ void recon_rs_block(const DevMesh& m, const DevParams& P, const float* __restrict__ Qf,
+                                               float* __restrict__ coef, int64_t c0, unsigned char* smem_raw) {
   using S = ReconSmemF<K, M, KM>;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
   float* tile = reinterpret_cast<float*>(smem_raw);                              // [kRows][kRC]
   float* snbr = reinterpret_cast<float*>(smem_raw + S::tile);                    // [5][K][kRC]
   float* sown = reinterpret_cast<float*>(smem_raw + S::tile + S::nbr);           // [5][kRC]
   float* sgeo = reinterpret_cast<float*>(smem_raw + S::tile + S::nbr + S::own);  // [7][kRC]
   uint8_t* ssub = smem_raw + S::tile + S::nbr + S::own + S::geo;                 // [M*KM][kRC]
-  if (m.nmesh == 1 && ctl->dt == 0.0) return;  // uniform over the grid (a batch computes every member)
   const int64_t nc = m.nc, ncp = m.ncp;
   const int t = threadIdx.x;
-  const int64_t c0 = (int64_t)blockIdx.x * kRC;
   const int nv = nc - c0 < kRC ? (int)(nc - c0) : kRC;  // cells of this block
   // With 5 warps of 32 lanes, thread (v, lane) stages column `lane` of the
   // rows v, v + 5, v + 10, ... of every per-cell array, so its addresses
@@ -1099,8 +1138,8 @@ __global__ void __launch_bounds__(kRThreads) k_recon_rs(DevMesh m, DevParams P, 
 #pragma unroll
   for (int i = 0; i < NE; ++i) {
     if (v + 5 * i <= K && live) {
-      qa[i] = __ldg(reinterpret_cast<const float4*>(Qf + 8 * (int64_t)jn[i]));
-      qb[i] = __ldg(Qf + 8 * (int64_t)jn[i] + 4);
+      qa[i] = ldro<COH>(reinterpret_cast<const float4*>(Qf + 8 * (int64_t)jn[i]));
+      qb[i] = ldro<COH>(Qf + 8 * (int64_t)jn[i] + 4);
     }
   }
   // 4. the first batch to binary32, then the remaining rows in batches
@@ -1184,8 +1223,16 @@ __global__ void __launch_bounds__(kRThreads) k_recon_rs(DevMesh m, DevParams P, 
   write_block_records<float>(tile, res, live, lane, v, nv, coef, c0);
 }
 
+template <int K, int M, int KM>
+__global__ void __launch_bounds__(kRThreads) k_recon_rs(DevMesh m, DevParams P, const float* __restrict__ Qf,
+                                                        float* __restrict__ coef, Control* __restrict__ ctl) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  if (m.nmesh == 1 && ctl->dt == 0.0) return;  // uniform over the grid (a batch computes every member)
+  recon_rs_block<K, M, KM>(m, P, Qf, coef, (int64_t)blockIdx.x * kRC, smem_raw);
+}
+
 // Point value and gradient of the combined polynomial of cell c at offset d.
-template <typename Real>
+template <typename Real, bool COH = false>
 __device__ __forceinline__ void eval_poly(const Real* __restrict__ coef, int64_t c, const Real d[3], Real val[5],
                                           Real grad[5][3]) {
   const Real dxx = d[0] * d[0], dyy = d[1] * d[1], dzz = d[2] * d[2];
@@ -1193,7 +1240,7 @@ __device__ __forceinline__ void eval_poly(const Real* __restrict__ coef, int64_t
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     Real p[10];
-    load10(coef + c * coef_rec<Real>() + v * 10, p);
+    load10<COH>(coef + c * coef_rec<Real>() + v * 10, p);
     const Real q = p[0], gx = p[1], gy = p[2], gz = p[3];
     const Real kxx = p[4], kyy = p[5], kzz = p[6], kxy = p[7], kyz = p[8], kzx = p[9];
     val[v] = q + gx * d[0] + gy * d[1] + gz * d[2] + kxx * dxx + kyy * dyy + kzz * dzz + kxy * dxy + kyz * dyz +
@@ -1215,22 +1262,24 @@ __device__ __forceinline__ void store_flux(float* __restrict__ Fs, int64_t f, co
 __device__ __forceinline__ void store_flux(double* __restrict__ Fs, int64_t f, const double x[10]) {
   store10(Fs + f * kFluxRec64, x);
 }
+template <bool COH = false>
 __device__ __forceinline__ void load_flux(const float* __restrict__ Fs, int64_t f, float x[10]) {
   const float4* r = reinterpret_cast<const float4*>(Fs + f * kFluxRec32);
-  const float4 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2);
+  const float4 a = ldro<COH>(r), b = ldro<COH>(r + 1), c = ldro<COH>(r + 2);
   x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
   x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
   x[8] = c.x; x[9] = c.y;
 }
+template <bool COH = false>
 __device__ __forceinline__ void load_flux(const double* __restrict__ Fs, int64_t f, double x[10]) {
-  load10(Fs + f * kFluxRec64, x);
+  load10<COH>(Fs + f * kFluxRec64, x);
 }
 
 // Flux of Gauss point g of face f (Eq. flux at one point of the face
 // quadrature), rotated back to the global frame and oriented from the owner
 // to the neighbour: r[0..4] = F, r[5..9] = dF/dt.  Returns the point's
 // quadrature weight times area.
-template <typename Real, int G, bool VISC>
+template <typename Real, int G, bool VISC, bool COH = false>
 __device__ __forceinline__ Real point_flux(const DevMesh& m, const DevParams& P, const FluxParams<Real>& FP,
                                            const Real* __restrict__ coef, int64_t f, int g, int64_t own, int nbr,
                                            Real dt, Real dt2i, Real r[10]) {
@@ -1246,7 +1295,7 @@ __device__ __forceinline__ Real point_flux(const DevMesh& m, const DevParams& P,
   for (int a = 0; a < 3; ++a) d[a] = cvt<Real>(m.fdl[(g * 3 + a) * nf + f]);
   const Real wgt = cvt<Real>(m.fw[g * nf + f]);
   Real qv[5], gr[5][3];
-  eval_poly(coef, own, d, qv, gr);
+  eval_poly<Real, COH>(coef, own, d, qv, gr);
   // local frame: rotate momentum, take derivatives along n, t1, t2
   Real ql[5], dl[3][5], qr[5], dr[3][5];
   auto rot = [&](const Real x[5], Real y[5]) {
@@ -1273,7 +1322,7 @@ __device__ __forceinline__ Real point_flux(const DevMesh& m, const DevParams& P,
   if (nbr >= 0) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) d[a] = cvt<Real>(m.fdr[(g * 3 + a) * nf + f]);
-    eval_poly(coef, (int64_t)nbr, d, qv, gr);
+    eval_poly<Real, COH>(coef, (int64_t)nbr, d, qv, gr);
     local(qv, gr, qr, dr);
   } else if (nbr == -3) {
     // no-slip adiabatic wall: mirror state, momentum reversed, normal
@@ -1314,19 +1363,13 @@ __device__ __forceinline__ Real point_flux(const DevMesh& m, const DevParams& P,
   return wgt;
 }
 
-// Face flux, one thread per face: sum over the Gauss points of weight*area
-// times the point flux.  Output: the flux record of each face (store_flux).
-// (binary32 register caps that fit without spilling, measured fastest:
-// inviscid 96 registers, 5 blocks per SM; with viscosity 168, 3 blocks per SM)
-template <typename Real, int G, bool VISC>
-__global__ void __launch_bounds__(kBlock, sizeof(Real) == 4 ? (VISC ? 3 : 5) : 1)
-    k_flux(DevMesh m, DevParams P, const Real* __restrict__ coef,
-                                                 Real* __restrict__ Fs, const Control* __restrict__ ctl) {
-  const int64_t nf = m.nf;
-  const int64_t f = (int64_t)blockIdx.x * kBlock + threadIdx.x;
-  if (f >= nf) return;
+// Face flux of face f: sum over the Gauss points of weight*area times the
+// point flux, stored as the face's flux record (store_flux).
+template <typename Real, int G, bool VISC, bool COH = false>
+__device__ __forceinline__ void flux_face(const DevMesh& m, const DevParams& P, const Real* __restrict__ coef,
+                                          Real* __restrict__ Fs, const Control* __restrict__ ctl, int64_t f) {
   const int64_t own = m.fown[f];
-  const double dtd = ctl[member_of(m, own)].dt;
+  const double dtd = ldm<COH>(&ctl[member_of(m, own)].dt);
   if (dtd == 0.0) return;
   const Real dt = cvt<Real>(dtd), dt2i = Real(2) / dt;
   const FluxParams<Real> FP = flux_params<Real>(P);
@@ -1337,11 +1380,23 @@ __global__ void __launch_bounds__(kBlock, sizeof(Real) == 4 ? (VISC ? 3 : 5) : 1
 #pragma unroll 1
   for (int g = 0; g < G; ++g) {
     Real r[10];
-    const Real w = point_flux<Real, G, VISC>(m, P, FP, coef, f, g, own, nbr, dt, dt2i, r);
+    const Real w = point_flux<Real, G, VISC, COH>(m, P, FP, coef, f, g, own, nbr, dt, dt2i, r);
 #pragma unroll
     for (int v = 0; v < 10; ++v) acc[v] = fma(w, r[v], acc[v]);
   }
   store_flux(Fs, f, acc);
+}
+
+// Face flux, one thread per face: sum over the Gauss points of weight*area
+// times the point flux.  Output: the flux record of each face (store_flux).
+// (binary32 register caps that fit without spilling, measured fastest:
+// inviscid 96 registers, 5 blocks per SM; with viscosity 168, 3 blocks per SM)
+template <typename Real, int G, bool VISC>
+__global__ void __launch_bounds__(kBlock, sizeof(Real) == 4 ? (VISC ? 3 : 5) : 1)
+    k_flux(DevMesh m, DevParams P, const Real* __restrict__ coef,
+                                                 Real* __restrict__ Fs, const Control* __restrict__ ctl) {
+  const int64_t f = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (f < m.nf) flux_face<Real, G, VISC>(m, P, coef, Fs, ctl, f);
 }
 
 // Face flux, one thread per Gauss point: the G points of a face run on G
@@ -1390,7 +1445,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_flux_gp(DevMesh m, DevParams P
 // (of F) and b (of dF/dt), with L = -a/|cell| and dL/dt = -b/|cell|.  The
 // face sum runs in the flux precision; the sums enter the S2O4 update in
 // binary64, where the factor -1/|cell| is folded into the stage coefficients.
-template <typename Real, int NFC>
+template <typename Real, int NFC, bool COH = false>
 __device__ __forceinline__ void gather(const DevMesh& m, const Real* __restrict__ Fs, int64_t c, double a[5],
                                        double b[5]) {
   Real sa[5] = {0, 0, 0, 0, 0}, sb[5] = {0, 0, 0, 0, 0};
@@ -1399,7 +1454,7 @@ __device__ __forceinline__ void gather(const DevMesh& m, const Real* __restrict_
     const int32_t e = m.cface[p * m.nc + c];
     const int64_t f = e >> 1;
     Real x[10];
-    load_flux(Fs, f, x);
+    load_flux<COH>(Fs, f, x);
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       sa[v] += (e & 1) ? -x[v] : x[v];
@@ -1419,6 +1474,25 @@ __device__ __forceinline__ void gather(const DevMesh& m, const Real* __restrict_
 }
 
 // Stage 1: Q* = Q + dt/2 L + dt^2/8 dL;  R = Q + dt L + dt^2/6 dL.
+template <typename Real, int NFC, bool COH = false>
+__device__ __forceinline__ void update1_cell(const DevMesh& m, const Real* __restrict__ Fs,
+                                             const double* __restrict__ Q, double* __restrict__ Qs,
+                                             double* __restrict__ R, float* __restrict__ Qf, double dt, int64_t c) {
+  double a[5], b[5];
+  gather<Real, NFC, COH>(m, Fs, c, a, b);
+  const double r1 = -dt * m.volinv[c], r2 = r1 * dt;  // dt L = r1 a, dt^2 dL = r2 b
+  const double h1 = 0.5 * r1, h2 = 0.125 * r2, k2 = r2 * (1.0 / 6.0);
+  double qs[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const double q = ldm<COH>(Q + v * m.nce + c);
+    qs[v] = fma(h2, b[v], fma(h1, a[v], q));
+    Qs[v * m.nce + c] = qs[v];
+    R[v * m.nc + c] = fma(k2, b[v], fma(r1, a[v], q));
+  }
+  if (Qf) store_qf(Qf, c, qs);
+}
+
 template <typename Real, int NFC>
 __global__ void __launch_bounds__(kBlock) k_update1(DevMesh m, const Real* __restrict__ Fs, const double* __restrict__ Q,
                                                    double* __restrict__ Qs, double* __restrict__ R,
@@ -1427,22 +1501,39 @@ __global__ void __launch_bounds__(kBlock) k_update1(DevMesh m, const Real* __res
   if (c >= m.nc) return;
   const double dt = ctl[member_of(m, c)].dt;
   if (dt == 0.0) return;
-  double a[5], b[5];
-  gather<Real, NFC>(m, Fs, c, a, b);
-  const double r1 = -dt * m.volinv[c], r2 = r1 * dt;  // dt L = r1 a, dt^2 dL = r2 b
-  const double h1 = 0.5 * r1, h2 = 0.125 * r2, k2 = r2 * (1.0 / 6.0);
-  double qs[5];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) {
-    const double q = Q[v * m.nce + c];
-    qs[v] = fma(h2, b[v], fma(h1, a[v], q));
-    Qs[v * m.nce + c] = qs[v];
-    R[v * m.nc + c] = fma(k2, b[v], fma(r1, a[v], q));
-  }
-  if (Qf) store_qf(Qf, c, qs);
+  update1_cell<Real, NFC>(m, Fs, Q, Qs, R, Qf, dt, c);
 }
 
-// Stage 2: Q^{n+1} = R + dt^2/3 dL(Q*); next step bound; non-finite flag.
+// Stage 2: Q^{n+1} = R + dt^2/3 dL(Q*); returns the cell's next step bound
+// (infinity when there is none) and flags a non-finite result.
+template <typename Real, int NFC, bool COH = false>
+__device__ __forceinline__ double update2_cell(const DevMesh& m, const DevParams& P, const Real* __restrict__ Fs,
+                                               double* __restrict__ Q, const double* __restrict__ R,
+                                               float* __restrict__ Qf, Control* __restrict__ ctl, int mid,
+                                               double dt, int64_t c) {
+  double a[5], b[5];
+  gather<Real, NFC, COH>(m, Fs, c, a, b);
+  const double k2 = -dt * dt * m.volinv[c] * (1.0 / 3.0);  // dt^2/3 dL = k2 b
+  double q[5];
+  bool finite = true;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    q[v] = fma(k2, b[v], ldm<COH>(R + v * m.nc + c));
+    finite = finite && isfinite(q[v]);
+    Q[v * m.nce + c] = q[v];
+  }
+  if (!finite) atomicOr(&ctl[mid].flags, FLAG_NONFINITE);
+  double bound;
+  if (Qf) {
+    float qf[5];
+    store_qf(Qf, c, q, qf);
+    bound = f2d(cell_dt_f(qf, cvt<float>(m.hdt[c]), P));
+  } else {
+    bound = cell_dt(q, m.hdt[c], P);
+  }
+  return (bound >= 0.0) ? bound : __longlong_as_double(0x7ff0000000000000LL);
+}
+
 template <typename Real, int NFC>
 __global__ void __launch_bounds__(kBlock) k_update2(DevMesh m, DevParams P, const Real* __restrict__ Fs,
                                                    double* __restrict__ Q, const double* __restrict__ R,
@@ -1452,28 +1543,7 @@ __global__ void __launch_bounds__(kBlock) k_update2(DevMesh m, DevParams P, cons
   double bound = __longlong_as_double(0x7ff0000000000000LL);
   const int mid = c < m.nc ? member_of(m, c) : -1;
   const double dt = mid >= 0 ? ctl[mid].dt : 0.0;
-  if (dt != 0.0) {
-    double a[5], b[5];
-    gather<Real, NFC>(m, Fs, c, a, b);
-    const double k2 = -dt * dt * m.volinv[c] * (1.0 / 3.0);  // dt^2/3 dL = k2 b
-    double q[5];
-    bool finite = true;
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      q[v] = fma(k2, b[v], R[v * m.nc + c]);
-      finite = finite && isfinite(q[v]);
-      Q[v * m.nce + c] = q[v];
-    }
-    if (!finite) atomicOr(&ctl[mid].flags, FLAG_NONFINITE);
-    if (Qf) {
-      float qf[5];
-      store_qf(Qf, c, q, qf);
-      bound = f2d(cell_dt_f(qf, cvt<float>(m.hdt[c]), P));
-    } else {
-      bound = cell_dt(q, m.hdt[c], P);
-    }
-    if (!(bound >= 0.0)) bound = __longlong_as_double(0x7ff0000000000000LL);
-  }
+  if (dt != 0.0) bound = update2_cell<Real, NFC>(m, P, Fs, Q, R, Qf, ctl, mid, dt, c);
   member_min_to(m, ctl, dt != 0.0 ? mid : -1, bound);
 }
 
@@ -1501,6 +1571,171 @@ __global__ void k_operator(DevMesh m, const Real* __restrict__ Fs, double* __res
   gather<Real, NFC>(m, Fs, c, a, b);
   const double vi = -m.volinv[c];
   for (int v = 0; v < 5; ++v) { L[v * m.nc + c] = a[v] * vi; dL[v * m.nc + c] = b[v] * vi; }
+}
+
+// --------------------------------------------------------------------------
+// Persistent steps (the batching of small meshes): one cooperative launch
+// advances every member of a solver by n S2O4 steps.  The phases of a step
+// are those of the separate kernels above (time step; then twice ghosts,
+// reconstruction, flux and update), run by the same device functions and
+// separated by grid-wide barriers.  Data that other blocks of the launch
+// wrote is read through L2 (COH = true loads).
+// --------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_volatile(const unsigned* p) {
+  return *reinterpret_cast<const volatile unsigned*>(p);
+}
+
+// Grid-wide barrier of a cooperative launch (all blocks are resident), with a
+// bounded wait: false after about 2^31 clock cycles (~1 s), with FLAG_TIMEOUT
+// set on member 0; the caller then leaves the kernel, and so does every
+// other block at its own bounded wait.
+__device__ bool grid_sync(GridBar* b, Control* ctl) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned g = ld_volatile(&b->gen);
+    __threadfence();
+    if (atomicAdd(&b->count, 1u) == gridDim.x - 1) {
+      atomicExch(&b->count, 0u);
+      __threadfence();
+      atomicAdd(&b->gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (ld_volatile(&b->gen) == g) {
+        if (clock64() - t0 > (1LL << 31)) {
+          atomicOr(&ctl->flags, FLAG_TIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <typename Real, int K, int M, int KM, int G, int NFC, bool VISC>
+__global__ void __launch_bounds__(kRThreads, sizeof(Real) == 4 ? 2 : 1)
+    k_persist(DevMesh m, DevParams P, DevWork w, int nsteps) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  constexpr bool F32 = sizeof(Real) == 4;
+  const double kInf = __longlong_as_double(0x7ff0000000000000LL);
+  Real* coef = static_cast<Real*>(w.coef);
+  Real* Fs = static_cast<Real*>(w.Fs);
+  float* Qf = F32 ? w.Qf : nullptr;
+  Control* ctl = w.ctl;
+  const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t ntiles = (m.nc + kRC - 1) / kRC;
+  for (int step = 0; step < nsteps; ++step) {
+    if (blockIdx.x == 0)
+      for (int i = threadIdx.x; i < m.nmesh; i += blockDim.x) finalize_one<true>(ctl + i, P.cfl);
+    if (!grid_sync(w.bar, ctl)) return;
+    const bool idle = m.nmesh == 1 && ldm<true>(&ctl->dt) == 0.0;  // the same in every block
+    for (int stage = 0; stage < 2; ++stage) {
+      double* Qin = stage == 0 ? w.Q : w.Qs;
+      if (m.ng) {
+        if (!idle)
+          for (int64_t g = gt; g < m.ng; g += nthr) ghost_one<true>(m, P, Qin, Qf, ctl, g);
+        if (!grid_sync(w.bar, ctl)) return;
+      }
+      if (!idle) {
+        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+          if constexpr (F32) recon_rs_block<K, M, KM, true>(m, P, w.Qf, coef, t * kRC, smem_raw);
+          else recon_block<Real, double, K, M, KM, false, true>(m, P, Qin, coef, ctl, t * kRC, smem_raw);
+          __syncthreads();  // the next tile reuses the shared memory
+        }
+      }
+      if (!grid_sync(w.bar, ctl)) return;
+      if (!idle)
+        for (int64_t f = gt; f < m.nf; f += nthr) flux_face<Real, G, VISC, true>(m, P, coef, Fs, ctl, f);
+      if (!grid_sync(w.bar, ctl)) return;
+      if (stage == 0) {
+        if (!idle)
+          for (int64_t c = gt; c < m.nc; c += nthr) {
+            const double dt = ldm<true>(&ctl[member_of(m, c)].dt);
+            if (dt != 0.0) update1_cell<Real, NFC, true>(m, Fs, w.Q, w.Qs, w.R, Qf, dt, c);
+          }
+      } else if (!idle) {
+        // whole blocks per round, so that every thread takes part in the
+        // block's step-bound reduction
+        for (int64_t c0 = (int64_t)blockIdx.x * blockDim.x; c0 < m.nc; c0 += nthr) {
+          const int64_t c = c0 + threadIdx.x;
+          const int mid = c < m.nc ? member_of(m, c) : -1;
+          const double dt = mid >= 0 ? ldm<true>(&ctl[mid].dt) : 0.0;
+          const double bound = dt != 0.0 ? update2_cell<Real, NFC, true>(m, P, Fs, w.Q, w.R, Qf, ctl, mid, dt, c)
+                                         : kInf;
+          member_min_to<kRThreads / 32>(m, ctl, dt != 0.0 ? mid : -1, bound);
+          __syncthreads();  // the reduction's shared buffer is reused
+        }
+      }
+      if (!grid_sync(w.bar, ctl)) return;
+    }
+  }
+}
+
+// Dynamic shared memory of the persistent kernel: the reconstruction tile.
+template <typename Real, int K, int M, int KM>
+constexpr size_t persist_smem() {
+  if constexpr (sizeof(Real) == 4) return ReconSmemF<K, M, KM>::bytes;
+  else return ReconSmem<Real, K, M, KM>::dq;
+}
+
+template <typename Real, int K, int M, int KM, int G, int NFC>
+cudaError_t persist_launch(const DevMesh& m, const DevParams& p, const DevWork& w, int n, cudaStream_t s,
+                           bool prep) {
+  const size_t smem = persist_smem<Real, K, M, KM>();
+  const void* fn = p.viscous ? (const void*)k_persist<Real, K, M, KM, G, NFC, true>
+                             : (const void*)k_persist<Real, K, M, KM, G, NFC, false>;
+  if (prep) {
+    cudaFuncSetAttribute(k_persist<Real, K, M, KM, G, NFC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    cudaFuncSetAttribute(k_persist<Real, K, M, KM, G, NFC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    return cudaSuccess;
+  }
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kRThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+  // no more blocks than the largest phase has units of work for
+  const int64_t want = std::max<int64_t>((m.nc + kRC - 1) / kRC, (m.nf + kRThreads - 1) / kRThreads);
+  const unsigned grid = (unsigned)std::min<int64_t>((int64_t)per_sm * sms, std::max<int64_t>(want, 1));
+  e = cudaMemsetAsync(w.bar, 0, sizeof(GridBar), s);
+  if (e != cudaSuccess) return e;
+  DevMesh mm = m;
+  DevParams pp = p;
+  DevWork ww = w;
+  int nn = n;
+  void* args[] = {&mm, &pp, &ww, &nn};
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kRThreads), args, smem, s);
+}
+
+template <typename Real>
+cudaError_t persist_any(const DevMesh& m, const DevParams& p, const DevWork& w, int n, cudaStream_t s,
+                        bool prep) {
+  if (m.M == 4) {
+    switch (m.K) {
+      case 12: return persist_launch<Real, 12, 4, 6, 3, 4>(m, p, w, n, s, prep);
+      case 13: return persist_launch<Real, 13, 4, 6, 3, 4>(m, p, w, n, s, prep);
+      case 14: return persist_launch<Real, 14, 4, 6, 3, 4>(m, p, w, n, s, prep);
+      case 15: return persist_launch<Real, 15, 4, 6, 3, 4>(m, p, w, n, s, prep);
+      case 16: return persist_launch<Real, 16, 4, 6, 3, 4>(m, p, w, n, s, prep);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  switch (m.K) {
+    case 18: return persist_launch<Real, 18, 8, 3, 4, 6>(m, p, w, n, s, prep);
+    case 20: return persist_launch<Real, 20, 8, 3, 4, 6>(m, p, w, n, s, prep);
+    case 22: return persist_launch<Real, 22, 8, 3, 4, 6>(m, p, w, n, s, prep);
+    case 24: return persist_launch<Real, 24, 8, 3, 4, 6>(m, p, w, n, s, prep);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 inline unsigned blocks(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
@@ -1659,8 +1894,19 @@ float time_stage(const DevMesh& m, const DevParams& p, const DevWork& w, int pre
 }
 
 void prepare_kernels(const DevMesh& m, int precision) {
-  if (precision == 1) recon_any<float, float>(m, DevParams{}, nullptr, nullptr, nullptr, 0, true);
-  else recon_any<double, double>(m, DevParams{}, nullptr, nullptr, nullptr, 0, true);
+  if (precision == 1) {
+    recon_any<float, float>(m, DevParams{}, nullptr, nullptr, nullptr, 0, true);
+    persist_any<float>(m, DevParams{}, DevWork{}, 0, 0, true);
+  } else {
+    recon_any<double, double>(m, DevParams{}, nullptr, nullptr, nullptr, 0, true);
+    persist_any<double>(m, DevParams{}, DevWork{}, 0, 0, true);
+  }
+}
+
+cudaError_t launch_persistent(const DevMesh& m, const DevParams& p, const DevWork& w, int precision, int n,
+                              cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  return precision == 1 ? persist_any<float>(m, p, w, n, s, false) : persist_any<double>(m, p, w, n, s, false);
 }
 
 void launch_control(const DevMesh& m, const DevWork& w, double t_end, double dt_fixed, cudaStream_t s) {

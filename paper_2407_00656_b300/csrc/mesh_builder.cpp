@@ -767,6 +767,7 @@ int64_t solver_work_bytes(const HostMesh& m, int precision, int nmesh) {
   b += al(rs * (f32 ? kCoefRec32 : kCoefRec64) * nc);  // reconstruction coefficients
   b += al(rs * (f32 ? kFluxRec32 : kFluxRec64) * nf);  // face flux and its time slope
   b += al((int64_t)sizeof(Control) * nmesh);  // control blocks
+  b += al((int64_t)sizeof(GridBar));           // barrier of the persistent step kernel
   return b + 256;
 }
 

@@ -46,7 +46,7 @@ class hgks_params(C.Structure):
         ("gamma", C.c_double), ("mu_ref", C.c_double), ("T_ref", C.c_double), ("visc_exp", C.c_double),
         ("Pr", C.c_double), ("cfl", C.c_double), ("tau_num_c", C.c_double), ("weno_eps", C.c_double),
         ("weno_gamma_lin", C.c_double), ("q_inf", C.c_double * 5), ("precision", C.c_int32),
-        ("use_graph", C.c_int32), ("autotune", C.c_int32), ("reserved", C.c_int32), ("stream", C.c_void_p),
+        ("use_graph", C.c_int32), ("autotune", C.c_int32), ("persistent", C.c_int32), ("stream", C.c_void_p),
     ]
 
 
