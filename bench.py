@@ -34,11 +34,11 @@ sys.path.insert(0, ROOT)
 
 # Executed binary64 operations per face of the FP64 flux kernel
 # k_flux<double, 3, inviscid> (sass dadd + dmul + 2 dfma per launch, divided
-# by the faces of the launch, ncu on the 12^3 x 6 mesh), and its DRAM bytes
-# per face (dram__bytes_read + dram__bytes_write of one launch on the
-# 40^3 x 6 mesh, 768,000 faces, larger than L2; the traffic grows with the
-# faces).  Set to None when the kernel changes until measured again.
-FP64_FLOPS_PER_FACE_INVISCID = 5038  # 104.47 Mflop per launch / 20736 faces
+# by the faces of the launch, ncu on the 32^3 x 6 mesh, 393,216 faces), and
+# its DRAM bytes per face (dram__bytes_read + dram__bytes_write of one launch
+# on the 40^3 x 6 mesh, 768,000 faces, larger than L2; the traffic grows with
+# the faces).  Set to None when the kernel changes until measured again.
+FP64_FLOPS_PER_FACE_INVISCID = 4990  # 1962.1 Mflop per launch / 393216 faces
 FP64_FLUX_DRAM_BYTES_PER_FACE = 469.0  # (312.29 + 47.90) MB / 768000 faces
 # Algorithmic bytes per cell of one binary32 reconstruction launch (k_recon_rs)
 # on tetrahedra: binary64 pseudo-inverse rows (9K + 3 M KM) x 8 B, sub-stencil
