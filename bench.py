@@ -155,7 +155,7 @@ def replica_throughput(cells: int, steps: int, world: int, seconds: float) -> fl
 
 
 def cpu_baseline(w, budget_steps: int = 3):
-    """The CPU checker as it stands, all host cores, on one step of the same mesh."""
+    """The CPU oracle as it stands, all host cores, on one step of the same mesh."""
     import oracle
 
     cores = os.cpu_count() or 1
@@ -173,7 +173,7 @@ def cpu_baseline(w, budget_steps: int = 3):
 
 
 def run_reference(args, rank, world):
-    """The CPU checker as it stands on the host cores (rank 0 only).  Each
+    """The CPU oracle as it stands on the host cores (rank 0 only).  Each
     timed step is one S2O4 step of a bounded sample of the workload: the
     24^3 x 6 jittered mesh for the density-wave workloads, the 6 x 24^2 x 31
     shell for the sphere workloads."""

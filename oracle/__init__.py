@@ -1,4 +1,4 @@
-"""CPU checker for the HGKS hot path: a plain FP64 statement of the scheme.
+"""CPU oracle for the HGKS hot path: a plain FP64 statement of the scheme.
 
 TEST INFRASTRUCTURE.  Only the test-suite, ``__graft_entry__.smoke()`` and the
 benchmark's CPU-baseline leg may import this package.  It shares no code with
@@ -104,7 +104,7 @@ def get_threads() -> int:
 
 
 class Oracle:
-    """One mesh and state on the CPU checker."""
+    """One mesh and state on the CPU oracle."""
 
     def __init__(self, xyz, cells, periods=None, bface_nodes=None, bface_tag=None, **params):
         lib = _load()

@@ -1,7 +1,7 @@
 // hgks_oracle.cpp -- plain, slow, FP64 CPU statement of the high-order
 // gas-kinetic scheme (HGKS) step on 3D unstructured tet/hex meshes.
 //
-// TEST INFRASTRUCTURE ONLY.  This file is the checker for the GPU library: it
+// TEST INFRASTRUCTURE ONLY.  This file is the oracle for the GPU library: it
 // shares no code with it, and only the test-suite, the smoke check and the
 // CPU-baseline leg of the benchmark may build, load or call it.  Every routine
 // cites the part of the paper (arXiv 2407.00656) it restates.

@@ -5,11 +5,15 @@
 //   k_ghost       boundary ghost cell averages (Algorithm 1 ghost cells)
 //   k_recon       third-order WENO reconstruction (Section 2.3, Eqs. polys,
 //                 weno), emitting one combined quadratic per cell and variable
+//                 (k_recon_rs: the binary32 form, staged through registers)
 //   k_flux        time-dependent gas-kinetic flux at the face Gauss points
-//                 (Section 2.1, Eq. flux; Section 2.2 linear-in-time fit)
+//                 (Section 2.1, Eq. flux; Section 2.2 linear-in-time fit), one
+//                 thread per face (k_flux_gp: one per Gauss point)
 //   k_update1/2   gather of the face fluxes per cell (no atomics) and the two
 //                 S2O4 stages (Section 2.2); stage 2 also produces the next
 //                 step bound and the non-finite flag
+//   k_persist     n whole steps in one cooperative launch, the phases above
+//                 separated by bounded grid-wide barriers
 //
 // Precision: Real = double (FP64) or float (FP32-mixed: reconstruction and
 // flux in binary32; geometry, pseudo-inverses and S2O4 sums in binary64).

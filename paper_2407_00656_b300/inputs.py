@@ -3,7 +3,7 @@
 This module holds no part of the gas-kinetic scheme. It only produces the data
 that a user would load from files: node coordinates, cell-to-node lists,
 boundary-face lists with their condition tags, and initial cell averages given
-by closed-form fields. Both the GPU library and the CPU checker consume these
+by closed-form fields. Both the GPU library and the CPU oracle consume these
 arrays as plain inputs.
 
 Workloads (Section 5 of the paper):

@@ -6,7 +6,7 @@ each half-line (split at u = 0 for the Heaviside factors), Gauss-Hermite in
 v and w, and Gauss-Laguerre in s (d^2 xi = pi ds).  Micro-slopes are solved
 with numpy from brute-force Gram matrices, the time integrals of Eq. (flux)
 use Gauss-Legendre in t, and F^n, dF/dt come from the 2x2 system of
-Section 2.2 solved by numpy.  Nothing here shares code with the checker.
+Section 2.2 solved by numpy.  Nothing here shares code with the oracle.
 """
 from __future__ import annotations
 

@@ -1,5 +1,5 @@
 """Accuracy configurations on the GPU path (Section 5.1): the 8^3 x 6 test
-run to t = 0.2 against the exact solution and the checker, and the precision
+run to t = 0.2 against the exact solution and the oracle, and the precision
 sweep over 12^3, 24^3, 48^3 x 6 jittered tets in FP64 and FP32-mixed:
 both converge at about third order, and the mixed solution differs from the
 FP64 one by at most 1e-5 in relative L1 (rho, rhoU, rhoE)."""
@@ -17,7 +17,7 @@ def l1(err, vol):
     return float((np.abs(err) * vol).sum() / vol.sum())
 
 
-def test_c1_to_t02_matches_checker_and_exact_solution():
+def test_c1_to_t02_matches_oracle_and_exact_solution():
     oracle.set_threads(8)
     xyz, cells, per = I.kuhn_cube(8)
     q0 = I.density_wave_state(xyz, cells, 0.0)

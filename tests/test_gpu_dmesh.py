@@ -56,3 +56,15 @@ def test_device_mesh_outlives_its_release_while_solvers_use_it():
     assert np.array_equal(got, want[0])
     s.close()
     ref.close()
+
+
+def test_default_flux_variant_follows_the_face_count():
+    """Per Gauss point on small meshes, per face on large ones (the crossovers
+    measured on B300: 16 blocks of 128 faces per SM in FP64, 2 in mixed)."""
+    small = I.kuhn_cube(6, jitter=0.1, seed=1)
+    large = I.kuhn_cube(40, jitter=0.1, seed=1)  # 768,000 faces
+    for precision in (H.HGKS_FP64, H.HGKS_FP32_MIXED):
+        for (xyz, cells, per), want in ((small, 1), (large, 0)):
+            s = H.Solver(H.Mesh(xyz, cells, per), I.uniform_state(len(cells)), precision=precision)
+            assert s.tuning == (want, 0), (precision, len(cells))
+            s.close()

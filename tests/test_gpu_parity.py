@@ -1,8 +1,8 @@
-"""GPU parity of libhgks against the CPU checker (FP64), element by element on
+"""GPU parity of libhgks against the CPU oracle (FP64), element by element on
 the same seeded inputs, through the C ABI.
 
 Tolerance (FP64 path): the one-step and stage-operator results must agree
-with the checker to 1e-11 relative to each variable's largest magnitude over
+with the oracle to 1e-11 relative to each variable's largest magnitude over
 the mesh.  Both sides evaluate the same formulas in binary64 in different
 orders (and with different, exactly equivalent, algebra for the moment sums),
 so they differ by accumulated rounding only; 1e-11 leaves about three orders
@@ -85,7 +85,7 @@ def test_stage_operator_sphere_shell_wall_and_far_field():
 
 
 @pytest.mark.parametrize("use_graph", [1, 0])
-def test_density_wave_steps_match_checker(use_graph):
+def test_density_wave_steps_match_oracle(use_graph):
     xyz, cells, per = I.kuhn_cube(8)  # 3072 cells, the accuracy-test mesh at 8^3
     q = I.density_wave_state(xyz, cells, 0.0)
     s, o = both(xyz, cells, per, q=q, use_graph=use_graph)

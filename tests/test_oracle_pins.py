@@ -1,6 +1,6 @@
-"""Pins of the CPU checker against what the paper and mathematics fix.
+"""Pins of the CPU oracle against what the paper and mathematics fix.
 
-Each test compares the checker with something other than itself: numerical
+Each test compares the oracle with something other than itself: numerical
 quadrature, closed forms from kinetic theory, analytic Euler / Navier-Stokes
 fluxes, or the Taylor expansion of the exact solution.
 """

@@ -1,4 +1,4 @@
-"""Whole-scheme pins of the CPU checker: reconstruction exactness, free-stream
+"""Whole-scheme pins of the CPU oracle: reconstruction exactness, free-stream
 preservation, conservation, convergence order on the exact density wave and
 consistency with the paper's accuracy table (Section 5.1)."""
 import os
