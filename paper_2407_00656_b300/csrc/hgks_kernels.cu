@@ -66,11 +66,14 @@ __device__ __forceinline__ double cvt<double>(double x) {
 }
 template <>
 __device__ __forceinline__ float cvt<float>(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
   const unsigned e = (hi >> 20) & 0x7ffu;
   const unsigned sign = hi & 0x80000000u;
-  const unsigned r = (sign | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29)) + ((lo >> 28) & 1u);
+  // (hi:lo) << 3 puts the low 9 exponent bits at [31:23] and the top 23
+  // mantissa bits below them; subtracting 896 << 23 (mod 2^32) rebiases the
+  // exponent, and the first dropped mantissa bit rounds
+  const unsigned fm = __funnelshift_l(lo, hi, 3);
+  const unsigned r = (((fm - (896u << 23)) & 0x7fffffffu) | sign) + ((lo >> 28) & 1u);
   return __uint_as_float(e < 897u ? sign : r);
 }
 
@@ -938,9 +941,17 @@ __device__ __forceinline__ void write_block_records(Real* smem, const Real res[1
   }
   __syncthreads();
   Real* dst = coef + c0 * REC;
+  // element e = l REC + r of the run; (l, r) advance by a constant step
+  constexpr int DL = kRThreads / REC, DR = kRThreads % REC;
+  int l = threadIdx.x / REC, r = threadIdx.x - (threadIdx.x / REC) * REC;
   for (int e = threadIdx.x; e < nv * REC; e += kRThreads) {
-    const int l = e / REC, r = e - l * REC;
     dst[e] = smem[l * PITCH + r];
+    l += DL;
+    r += DR;
+    if (r >= REC) {
+      r -= REC;
+      ++l;
+    }
   }
 }
 
@@ -1125,17 +1136,21 @@ __device__ __forceinline__ void recon_rs_block(const DevMesh& m, const DevParams
     const int k = v + 5 * i;
     jn[i] = (k < K && live) ? __ldcs(m.sten + (int64_t)k * nc + c0 + lane) : (int32_t)(c0 + lane);
   }
-  // 2. first batch of pseudo-inverse rows (binary64, read once: streaming loads)
+  // 2. first batch of pseudo-inverse rows (binary64, read once: streaming
+  // loads).  Thread (v, lane) copies rows v + 5 j: J0 rows of pinv0 for
+  // every v, then one more row for v < T0 (likewise J1, T1 for pinvm); the
+  // row counts are compile-time constants, so only the tail row is guarded.
   constexpr int R0 = 9 * K, R1 = M * 3 * KM;  // rows of pinv0 and pinvm
-  constexpr int N0 = (R0 + 4) / 5, N1 = (R1 + 4) / 5;
+  constexpr int J0 = R0 / 5, T0 = R0 - 5 * J0, J1 = R1 / 5, T1 = R1 - 5 * J1;
   constexpr int B = 8;
-  const double* p0 = m.pinv0 + (int64_t)v * ncp + c0 + lane;
-  const double* p1 = m.pinvm + (int64_t)v * ncp + c0 + lane;
+  static_assert(J0 >= B, "the first batch is a full one");
+  constexpr int RS = 5 * kRC;  // shared-memory stride between a thread's rows
   const int64_t step = 5 * ncp;
+  const double* p0 = m.pinv0 + (int64_t)v * ncp + c0 + lane;
+  float* d0 = tile + v * kRC + lane;
   double pv[B];
 #pragma unroll
-  for (int i = 0; i < B; ++i)
-    if (i < N0 && v + 5 * i < R0) pv[i] = __ldcs(p0 + i * step);
+  for (int i = 0; i < B; ++i) pv[i] = __ldcs(p0 + i * step);
   // 3. neighbour and own state records (32 bytes each)
   float4 qa[NE];
   float qb[NE];
@@ -1148,25 +1163,45 @@ __device__ __forceinline__ void recon_rs_block(const DevMesh& m, const DevParams
   }
   // 4. the first batch to binary32, then the remaining rows in batches
 #pragma unroll
-  for (int i = 0; i < B; ++i)
-    if (i < N0 && v + 5 * i < R0) tile[(v + 5 * i) * kRC + lane] = cvt<float>(pv[i]);
+  for (int i = 0; i < B; ++i) d0[i * RS] = cvt<float>(pv[i]);
+  {
+    const double* q = p0 + B * step;
+    float* d = d0 + B * RS;
 #pragma unroll 1
-  for (int i0 = B; i0 < N0; i0 += B) {
+    for (int j = B; j + B <= J0; j += B) {
 #pragma unroll
-    for (int i = 0; i < B; ++i)
-      if (i0 + i < N0 && v + 5 * (i0 + i) < R0) pv[i] = __ldcs(p0 + (i0 + i) * step);
+      for (int i = 0; i < B; ++i) pv[i] = __ldcs(q + i * step);
 #pragma unroll
-    for (int i = 0; i < B; ++i)
-      if (i0 + i < N0 && v + 5 * (i0 + i) < R0) tile[(v + 5 * (i0 + i)) * kRC + lane] = cvt<float>(pv[i]);
+      for (int i = 0; i < B; ++i) d[i * RS] = cvt<float>(pv[i]);
+      q += B * step;
+      d += B * RS;
+    }
+    constexpr int REM0 = (J0 - B) % B;
+#pragma unroll
+    for (int i = 0; i < REM0; ++i) pv[i] = __ldcs(q + i * step);
+#pragma unroll
+    for (int i = 0; i < REM0; ++i) d[i * RS] = cvt<float>(pv[i]);
+    if (v < T0) tile[(5 * J0 + v) * kRC + lane] = cvt<float>(__ldcs(p0 + J0 * step));
   }
+  {
+    const double* p1 = m.pinvm + (int64_t)v * ncp + c0 + lane;
+    const double* q = p1;
+    float* d = d0 + R0 * kRC;
 #pragma unroll 1
-  for (int i0 = 0; i0 < N1; i0 += B) {
+    for (int j = 0; j + B <= J1; j += B) {
 #pragma unroll
-    for (int i = 0; i < B; ++i)
-      if (i0 + i < N1 && v + 5 * (i0 + i) < R1) pv[i] = __ldcs(p1 + (i0 + i) * step);
+      for (int i = 0; i < B; ++i) pv[i] = __ldcs(q + i * step);
 #pragma unroll
-    for (int i = 0; i < B; ++i)
-      if (i0 + i < N1 && v + 5 * (i0 + i) < R1) tile[(R0 + v + 5 * (i0 + i)) * kRC + lane] = cvt<float>(pv[i]);
+      for (int i = 0; i < B; ++i) d[i * RS] = cvt<float>(pv[i]);
+      q += B * step;
+      d += B * RS;
+    }
+    constexpr int REM1 = J1 % B;
+#pragma unroll
+    for (int i = 0; i < REM1; ++i) pv[i] = __ldcs(q + i * step);
+#pragma unroll
+    for (int i = 0; i < REM1; ++i) d[i * RS] = cvt<float>(pv[i]);
+    if (v < T1) tile[(R0 + 5 * J1 + v) * kRC + lane] = cvt<float>(__ldcs(p1 + J1 * step));
   }
   // 5. neighbour states to shared memory ([5][K][kRC]; own states [5][kRC])
 #pragma unroll
