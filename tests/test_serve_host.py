@@ -22,3 +22,124 @@ def test_c5_stream_shape():
     res = [r.params["mu_ref"] and 0.2535 / r.params["mu_ref"] for r in reqs if r.kind == "sphere"]
     assert all(99.9 <= re <= 300.1 for re in res)
     assert all(r.steps == 200 for r in reqs)
+
+
+# ---------------------------------------------------------------------------
+# The scheduling logic of Server.run on the host, with the library replaced
+# by fakes: a solver "finishes" a chunk after a few polls, device meshes and
+# solvers report sizes from a formula.  This checks admission by memory,
+# eviction of idle device meshes, batching rules and completion, without a GPU.
+# ---------------------------------------------------------------------------
+import types
+
+
+class _FakeMesh:
+    def __init__(self, cells):
+        self.n_cells = cells
+        self.static_bytes = 100 * cells
+        self._work = 10 * cells
+
+    def work_bytes(self, precision):
+        return self._work
+
+    def device_bytes(self, precision):
+        return self.static_bytes + self._work
+
+    def clone(self):
+        return self
+
+
+class _FakeCache:
+    def __init__(self, cells_of):
+        self.cells_of = cells_of
+        self.meshes = {}
+
+    def peek(self, kind, size):
+        key = (kind, size)
+        if key not in self.meshes:
+            self.meshes[key] = (_FakeMesh(self.cells_of(kind, size)), np.zeros((1, 5)))
+        return self.meshes[key]
+
+
+def _fake_hgks(log):
+    class DeviceMesh:
+        live = 0
+
+        def __init__(self, mesh):
+            DeviceMesh.live += 1
+            log.append(("dmesh", mesh.n_cells))
+            self.n_cells = mesh.n_cells
+
+        def release(self):
+            DeviceMesh.live -= 1
+            log.append(("release", self.n_cells))
+
+    class Solver:
+        def __init__(self, mesh, q, precision=None, **kw):
+            if isinstance(mesh, list):
+                self.member_cells = [m.n_cells for m in mesh]
+                log.append(("batch", tuple(self.member_cells)))
+            else:
+                self.member_cells = [mesh.n_cells]
+            self.n_cells = self.member_cells[0]
+            self.device_bytes = sum(110 * c for c in self.member_cells)
+            self.steps = 0
+            self.polls = 0
+
+        def set_tuning(self, f, r):
+            self.tuning = (f, r)
+
+        def query(self):
+            self.polls += 1
+            return self.polls % 3 == 0
+
+        def step(self, k):
+            self.steps += k
+
+        def member_read(self, i):
+            return np.full((self.member_cells[i], 5), float(self.steps)), 0.1 * self.steps, self.steps
+
+        def close(self):
+            pass
+
+    return types.SimpleNamespace(DeviceMesh=DeviceMesh, Solver=Solver, HGKS_FP32_MIXED=1, HGKS_FP64=0)
+
+
+def _requests():
+    reqs = []
+    for i, (kind, size) in enumerate([("density", 1), ("density", 2), ("sphere", 3), ("density", 1),
+                                      ("sphere", 4), ("density", 2), ("sphere", 3), ("density", 5)]):
+        reqs.append(S.Request(i, 0.0, kind, size, 30, {} if kind == "density" else {"mu_ref": 1e-3}))
+    return reqs
+
+
+def _cells(kind, size):
+    return {("density", 1): 500, ("density", 2): 800, ("sphere", 3): 20000, ("sphere", 4): 30000,
+            ("density", 5): 40000}[(kind, size)]
+
+
+def test_server_logic_with_fake_solvers(monkeypatch):
+    log = []
+    monkeypatch.setattr(S, "H", _fake_hgks(log))
+    cache = _FakeCache(_cells)
+    # room for the small batch and for one large solve with its mesh at a time
+    budget = 110 * 40000 + 110 * 1600 + 65536 * 4
+    server = S.Server(mem_budget=budget, chunk_steps=7, small_cells=1000, max_batch=3, batch_cells=1500,
+                      cache=cache)
+    reqs = server.run(_requests(), time_limit=60)
+    assert all(r.steps_done == 30 for r in reqs) and all(r.finished >= r.admitted >= 0 for r in reqs)
+    assert server.peak_used <= budget
+    # small requests were batched, by kind and parameters, within the caps
+    batches = [e[1] for e in log if e[0] == "batch"]
+    assert batches and all(len(b) <= 3 and sum(b) <= 1500 for b in batches)
+    # large geometries got device meshes, and memory pressure evicted idle ones
+    made = [e[1] for e in log if e[0] == "dmesh"]
+    assert set(made) == {20000, 30000, 40000}
+    first_release = min(i for i, e in enumerate(log) if e[0] == "release")
+    last_dmesh = max(i for i, e in enumerate(log) if e[0] == "dmesh")
+    assert first_release < last_dmesh
+    # every device mesh is released when the run ends
+    assert S.H.DeviceMesh.live == 0
+    # the sphere 3 geometry is shared by its two requests unless evicted between them
+    assert made.count(20000) <= 2
+    assert all(getattr(r, "cells") in (500, 800, 20000, 30000, 40000) for r in reqs)
