@@ -38,7 +38,7 @@ sys.path.insert(0, ROOT)
 # its DRAM bytes per face (dram__bytes_read + dram__bytes_write of one launch
 # on the 40^3 x 6 mesh, 768,000 faces, larger than L2; the traffic grows with
 # the faces).  Set to None when the kernel changes until measured again.
-FP64_FLOPS_PER_FACE_INVISCID = 4990  # 1962.1 Mflop per launch / 393216 faces
+FP64_FLOPS_PER_FACE_INVISCID = 4786  # 1881.9 Mflop per launch / 393216 faces
 FP64_FLUX_DRAM_BYTES_PER_FACE = 469.0  # (312.29 + 47.90) MB / 768000 faces
 # Algorithmic bytes per cell of one binary32 reconstruction launch (k_recon_rs)
 # on tetrahedra: binary64 pseudo-inverse rows (9K + 3 M KM) x 8 B, sub-stencil
