@@ -102,11 +102,15 @@ typedef struct {
  *   persistent     1: hgks_step runs its n steps as one persistent
  *                  cooperative launch (every phase of every step in one
  *                  kernel, grid-wide barriers between phases) instead of n
- *                  graph launches; for small meshes and batches of them,
- *                  where a step is a few short kernels.  Results agree with
- *                  the separate kernels to a few units in the last place.
- *                  A grid barrier that waits more than about a second ends
- *                  the launch with HGKS_ETIMEOUT at the next sync or read.
+ *                  graph launches, for small meshes and batches of them;
+ *                  measured slower than graph launches on B300, so off by
+ *                  default.  The flux runs per face and the reconstruction
+ *                  variants are fixed (binary32: register-staged; binary64:
+ *                  rows read directly), whatever hgks_set_tuning selected.
+ *                  Results agree with the separate kernels to a few units in
+ *                  the last place.  A grid barrier that waits more than
+ *                  about a second ends the launch with HGKS_ETIMEOUT at the
+ *                  next sync or read.
  *   stream         cudaStream_t to run on, or NULL for a library stream. */
 typedef struct {
   double gamma, mu_ref, T_ref, visc_exp, Pr, cfl, tau_num_c, weno_eps, weno_gamma_lin;
