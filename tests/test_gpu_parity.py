@@ -69,19 +69,39 @@ def test_stage_operator_viscous_jittered_tets(kw):
     assert relerr(dL, dLo) < TOL
 
 
-def test_stage_operator_sphere_shell_wall_and_far_field():
+@pytest.mark.parametrize("mach", [0.2535, 1.5])
+def test_stage_operator_sphere_shell_wall_and_far_field(mach):
+    """Hexahedra, no-slip wall, far field (at Ma 1.5 the far field has
+    supersonic inflow upstream and supersonic outflow downstream), viscous
+    with the power law and numerical collision time."""
     xyz, cells, bfn, bft = I.sphere_shell(6, 5, r_far=4.0, jitter=0.2, seed=3)
-    qinf = I.free_stream(0.2535)
+    qinf = I.free_stream(mach)
     rng = np.random.default_rng(0)
     q = np.tile(qinf, (len(cells), 1))
     q[:, 0] *= 1 + 0.05 * rng.uniform(-1, 1, len(cells))
     q[:, 1:4] += 0.05 * rng.uniform(-1, 1, (len(cells), 3))
-    s, o = both(xyz, cells, None, bfn, bft, q=q, qinf=qinf, mu_ref=0.2535 / 300, Pr=0.72, visc_exp=0.7,
+    s, o = both(xyz, cells, None, bfn, bft, q=q, qinf=qinf, mu_ref=mach / 300, Pr=0.72, visc_exp=0.7,
                 T_ref=1 / 1.4, tau_c=1.0)
     L, dL = s.stage_operator(5e-3)
     Lo, dLo = o.operator(5e-3)
     assert relerr(L, Lo) < TOL
     assert relerr(dL, dLo) < TOL
+
+
+def test_sphere_shell_steps_match_oracle():
+    """Three full S2O4 steps on hexahedra with wall and far-field ghosts."""
+    xyz, cells, bfn, bft = I.sphere_shell(5, 4, r_far=3.0, jitter=0.15, seed=5)
+    qinf = I.free_stream(0.2535)
+    q = np.tile(qinf, (len(cells), 1))
+    q[:, 0] *= 1 + 0.03 * np.sin(np.arange(len(cells)))
+    s, o = both(xyz, cells, None, bfn, bft, q=q, qinf=qinf, mu_ref=0.2535 / 200, Pr=0.72, visc_exp=0.7,
+                T_ref=1 / 1.4, tau_c=1.0)
+    s.step(3)
+    o.step(3)
+    qg, tg, ng = s.read()
+    qo, to, no = o.get_state()
+    assert ng == no == 3 and abs(tg - to) <= 1e-12 * to
+    assert relerr(qg, qo) < TOL
 
 
 @pytest.mark.parametrize("use_graph", [1, 0])
