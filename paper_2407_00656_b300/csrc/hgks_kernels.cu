@@ -1239,27 +1239,65 @@ __device__ __forceinline__ void recon_rs_block(const DevMesh& m, const DevParams
 #pragma unroll
   for (int k = 0; k < K; ++k) dq[k] = snbr[(v * K + k) * kRC + lane] - qv;
   auto row = [&](int r) -> float { return tile[r * kRC + lane]; };
-  // least-squares polynomials (the operation order of k_recon)
+  // least-squares polynomials (the operation order of k_recon).  On
+  // hexahedra, pairs of output rows advance together in packed binary32 FMAs
+  // (two independent round-to-nearest FMAs per instruction: the same
+  // results); measured 8% faster there and 5% slower on tetrahedra.
   float a[9];
+  float b[M][3];
+  if constexpr (M == 8) {
+    float2 dq2[K];
 #pragma unroll
-  for (int d = 0; d < 9; ++d) {
+    for (int k = 0; k < K; ++k) dq2[k] = make_float2(dq[k], dq[k]);
+#pragma unroll
+    for (int d = 0; d < 8; d += 2) {
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc = __ffma2_rn(make_float2(row(d * K + k), row((d + 1) * K + k)), dq2[k], acc);
+      a[d] = acc.x;
+      a[d + 1] = acc.y;
+    }
     float sacc = 0.f;
 #pragma unroll
-    for (int k = 0; k < K; ++k) sacc += row(d * K + k) * dq[k];
-    a[d] = sacc;
-  }
-  float b[M][3];
+    for (int k = 0; k < K; ++k) sacc = fmaf(row(8 * K + k), dq[k], sacc);
+    a[8] = sacc;
 #pragma unroll
-  for (int s = 0; s < M; ++s) {
-    float x[KM];
+    for (int s = 0; s < M; ++s) {
+      float x[KM];
 #pragma unroll
-    for (int r = 0; r < KM; ++r) x[r] = snbr[(v * K + ssub[(s * KM + r) * kRC + lane]) * kRC + lane] - qv;
+      for (int r = 0; r < KM; ++r) x[r] = snbr[(v * K + ssub[(s * KM + r) * kRC + lane]) * kRC + lane] - qv;
+      float2 acc = make_float2(0.f, 0.f);
+      float acc2 = 0.f;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      float acc = 0.f;
+      for (int r = 0; r < KM; ++r) {
+        acc = __ffma2_rn(make_float2(row(9 * K + (s * 3) * KM + r), row(9 * K + (s * 3 + 1) * KM + r)),
+                         make_float2(x[r], x[r]), acc);
+        acc2 = fmaf(row(9 * K + (s * 3 + 2) * KM + r), x[r], acc2);
+      }
+      b[s][0] = acc.x;
+      b[s][1] = acc.y;
+      b[s][2] = acc2;
+    }
+  } else {
 #pragma unroll
-      for (int r = 0; r < KM; ++r) acc += row(9 * K + (s * 3 + d) * KM + r) * x[r];
-      b[s][d] = acc;
+    for (int d = 0; d < 9; ++d) {
+      float sacc = 0.f;
+#pragma unroll
+      for (int k = 0; k < K; ++k) sacc += row(d * K + k) * dq[k];
+      a[d] = sacc;
+    }
+#pragma unroll
+    for (int s = 0; s < M; ++s) {
+      float x[KM];
+#pragma unroll
+      for (int r = 0; r < KM; ++r) x[r] = snbr[(v * K + ssub[(s * KM + r) * kRC + lane]) * kRC + lane] - qv;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        float acc = 0.f;
+#pragma unroll
+        for (int r = 0; r < KM; ++r) acc += row(9 * K + (s * 3 + d) * KM + r) * x[r];
+        b[s][d] = acc;
+      }
     }
   }
   float mi[6];
