@@ -6,11 +6,13 @@ step (time step, two stages of reconstruction, flux and update) of the whole
 mesh.  Metric: cell-updates/s = cells x steps / device time.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hgks|reference]
-                    [--precision fp64|mixed] [--workload densityN | densityNv | sphere | sphereN]
+                    [--precision fp64|mixed]
+                    [--workload densityN | densityNv | sphere | sphereN | transonic | transonicN]
                     [--no-cpu-baseline] [--no-serve] [--serve]
 
 densityN: N^3 x 6 tets (densityNv with mu = 1e-3, Pr = 0.72); sphere: the
-1.51M-cell hex shell at Ma 0.2535, Re 300; sphereN: a 6 x N^2 x 1.3N shell.
+1.51M-cell hex shell at Ma 0.2535, Re 300; sphereN: a 6 x N^2 x 1.3N shell;
+transonic, transonicN: the same shells at Ma 1.5, Re 300.
 
 Prints one JSON line (rank 0).  For N > 1 (torchrun) every rank advances its
 own replica of the workload: the path has no exchange step on one GPU per
@@ -79,15 +81,20 @@ def workload(name: str):
         return dict(xyz=xyz, cells=cells, periods=per, q=q, params=params,
                     desc=f"density wave, {n}^3 x 6 tets" + (", jitter 0.15h seed 0" if jit else "") +
                     (", mu 1e-3 Pr 0.72" if visc else ", inviscid"))
-    # sphere: the 1.51M-cell shell 6 x 58^2 x 75; sphereN: 6 x N^2 x round(1.3 N)
-    if name == "sphere" or (name.startswith("sphere") and name[len("sphere"):].isdigit()):
-        n, nr = (58, 75) if name == "sphere" else (int(name[len("sphere"):]), max(2, round(1.3 * int(name[len("sphere"):]))))
-        xyz, cells, bfn, bft = I.sphere_shell(n, nr, seed=0)
-        qinf = I.free_stream(0.2535)
-        q = np.tile(qinf, (len(cells), 1))
-        return dict(xyz=xyz, cells=cells, periods=None, bfn=bfn, bft=bft, q=q,
-                    params=dict(q_inf=qinf, mu_ref=0.2535 / 300, Pr=0.72, visc_exp=0.7, T_ref=1 / 1.4, tau_num_c=1.0),
-                    desc=f"sphere shell 6x{n}^2x{nr} hex, Ma 0.2535 Re 300, wall + far field")
+    # sphere: the 1.51M-cell shell 6 x 58^2 x 75 at Ma 0.2535, Re 300;
+    # sphereN: 6 x N^2 x round(1.3 N); transonic, transonicN: the same shells
+    # at Ma 1.5, Re 300 (the transonic sphere of Section 5.2)
+    for base, mach in (("sphere", 0.2535), ("transonic", 1.5)):
+        size = name[len(base):] if name.startswith(base) else None
+        if size == "" or (size and size.isdigit()):
+            n, nr = (58, 75) if size == "" else (int(size), max(2, round(1.3 * int(size))))
+            xyz, cells, bfn, bft = I.sphere_shell(n, nr, seed=0)
+            qinf = I.free_stream(mach)
+            q = np.tile(qinf, (len(cells), 1))
+            return dict(xyz=xyz, cells=cells, periods=None, bfn=bfn, bft=bft, q=q,
+                        params=dict(q_inf=qinf, mu_ref=mach / 300, Pr=0.72, visc_exp=0.7, T_ref=1 / 1.4,
+                                    tau_num_c=1.0),
+                        desc=f"sphere shell 6x{n}^2x{nr} hex, Ma {mach} Re 300, wall + far field")
     raise ValueError(name)
 
 
@@ -176,7 +183,7 @@ def run_reference(args, rank, world):
     """The CPU oracle as it stands on the host cores (rank 0 only).  Each
     timed step is one S2O4 step of a bounded sample of the workload: the
     24^3 x 6 jittered mesh for the density-wave workloads, the 6 x 24^2 x 31
-    shell for the sphere workloads."""
+    shell at the workload's Mach number for the sphere workloads."""
     if rank != 0:
         return
     import oracle
@@ -187,6 +194,8 @@ def run_reference(args, rank, world):
         ws = workload("density24v" if args.workload.endswith("v") else "density24")
     elif args.workload.startswith("sphere"):
         ws = workload("sphere24")
+    elif args.workload.startswith("transonic"):
+        ws = workload("transonic24")
     cores = os.cpu_count() or 1
     oracle.set_threads(cores)
     o = oracle.Oracle(ws["xyz"], ws["cells"], ws["periods"], ws.get("bfn"), ws.get("bft"),
