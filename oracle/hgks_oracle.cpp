@@ -1,5 +1,5 @@
 // hgks_oracle.cpp -- plain, slow, FP64 CPU statement of the high-order
-// gas-kinetic scheme (HGKS) step on 3D unstructured tet/hex meshes.
+// gas-kinetic scheme (HGKS) step on 3D unstructured tet/hex/prism meshes.
 //
 // TEST INFRASTRUCTURE ONLY.  This file is the oracle for the GPU library: it
 // shares no code with it, and only the test-suite, the smoke check and the
@@ -560,7 +560,7 @@ struct Face {
 
 // One member of a stencil as seen from the target cell.
 struct Ref {
-  int kind = 0;    // 0: cell (maybe a periodic image), 1: ghost
+  int kind = 0;    // 0: cell (maybe a periodic image), 1: ghost, -1: none (collapsed face)
   int id = -1;     // cell index (for ghosts: the interior cell mirrored)
   int face = -1;   // ghost: boundary face of the mirror
   V3 shift = {0, 0, 0};
@@ -573,11 +573,12 @@ struct Ref {
 
 struct Cell {
   int type;           // 4 or 8
+  bool prism = false; // type 8 with nodes 2 = 3 and 6 = 7 (a triangular prism)
   int nodes[8];
   double vol, h, hdt;
   V3 cen;
   double mom[6];      // central second moments: xx yy zz xy yz zx (averages)
-  int face[6];
+  int face[6];        // -1: the collapsed side of a prism (no face)
   int side[6];        // +1 owner, -1 neighbour
   Ref nb[6];
   std::vector<Ref> big;                // big stencil, excluding the cell itself
@@ -766,6 +767,19 @@ static bool build_mesh(Solver& S, int64_t n_nodes, const double* xyz, int64_t n_
     int64_t base = cell_ptr ? cell_ptr[c] : c * (int64_t)cl.type;
     if (cl.type != 4 && cl.type != 8) { S.err = "unsupported cell type"; return false; }
     for (int a = 0; a < cl.type; ++a) cl.nodes[a] = (int)cell_nodes[base + a];
+    if (cl.type == 8) {
+      // READING (prisms; the paper defines hexahedra and tetrahedra only): a
+      // triangular prism is given as a hexahedron with nodes 2 = 3 and 6 = 7;
+      // its side face 4 (nodes 2 3 7 6) collapses to an edge and is dropped.
+      int distinct = 0;
+      for (int a = 0; a < 8; ++a) {
+        bool seen = false;
+        for (int b = 0; b < a; ++b) seen = seen || cl.nodes[b] == cl.nodes[a];
+        distinct += !seen;
+      }
+      cl.prism = cl.nodes[2] == cl.nodes[3] && cl.nodes[6] == cl.nodes[7];
+      if (distinct != (cl.prism ? 6 : 8)) { S.err = "unsupported degenerate hexahedron"; return false; }
+    }
     V3 p[8];
     for (int a = 0; a < cl.type; ++a) p[a] = S.X[cl.nodes[a]];
     if (cl.type == 4) mom_tet(p, cl.vol, cl.cen, cl.mom);
@@ -782,6 +796,15 @@ static bool build_mesh(Solver& S, int64_t n_nodes, const double* xyz, int64_t n_
       Face f;
       f.nn = cl.type == 4 ? 3 : 4;
       for (int a = 0; a < f.nn; ++a) f.nodes[a] = cl.nodes[cl.type == 4 ? TET_FACE[p][a] : HEX_FACE[p][a]];
+      if (cl.prism) {
+        if (p == 3) { cl.face[p] = -1; cl.side[p] = 0; continue; }  // collapsed to the edge 2-6
+        // the prism's bottom and top quads (nodes 0 1 2 2, 4 5 6 6) are
+        // triangles: drop the repeated node
+        int nn = 0;
+        for (int a = 0; a < 4; ++a)
+          if (nn == 0 || (f.nodes[a] != f.nodes[nn - 1] && (a < 3 || f.nodes[a] != f.nodes[0]))) f.nodes[nn++] = f.nodes[a];
+        f.nn = nn;
+      }
       std::array<int, 4> key = {-1, -1, -1, -1};
       for (int a = 0; a < f.nn; ++a) key[a] = f.nodes[a];
       std::sort(key.begin(), key.begin() + f.nn);
@@ -865,7 +888,8 @@ static bool build_mesh(Solver& S, int64_t n_nodes, const double* xyz, int64_t n_
   S.F.swap(nfv);
   for (auto& cl : S.C) {
     int nf = cl.type == 4 ? 4 : 6;
-    for (int p = 0; p < nf; ++p) cl.face[p] = remap[cl.face[p]];
+    for (int p = 0; p < nf; ++p)
+      if (cl.face[p] >= 0) cl.face[p] = remap[cl.face[p]];
   }
   // CellNeighbor (Section 3.1, item 3); boundary faces give ghost members
   for (int c = 0; c < (int)S.C.size(); ++c) {
@@ -873,6 +897,7 @@ static bool build_mesh(Solver& S, int64_t n_nodes, const double* xyz, int64_t n_
     int nf = cl.type == 4 ? 4 : 6;
     double area = 0.0;
     for (int p = 0; p < nf; ++p) {
+      if (cl.face[p] < 0) { cl.nb[p].kind = -1; continue; }
       const Face& f = S.F[cl.face[p]];
       for (int g = 0; g < f.ng; ++g) area += f.wa[g];
       Ref r;
@@ -898,7 +923,7 @@ static bool build_stencils(Solver& S) {
     int nf = cl.type == 4 ? 4 : 6;
     self.kind = 0; self.id = c; self.face = -1; self.shift = {0, 0, 0};
     auto find_or_add = [&](const Ref& r) -> int {
-      if (r.same(self)) return -1;
+      if (r.kind < 0 || r.same(self)) return -1;
       for (int k = 0; k < (int)cl.big.size(); ++k) if (cl.big[k].same(r)) return k;
       cl.big.push_back(r);
       return (int)cl.big.size() - 1;
@@ -913,6 +938,7 @@ static bool build_stencils(Solver& S) {
       for (int q = 0; q < nf2; ++q) find_or_add(neighbour_of(S, r, q));
     }
     auto idx = [&](const Ref& r) {
+      if (r.kind < 0) return -1;
       for (int k = 0; k < (int)cl.big.size(); ++k) if (cl.big[k].same(r)) return k;
       return -1;
     };
@@ -936,13 +962,18 @@ static bool build_stencils(Solver& S) {
         cl.sub.push_back(s);
       }
     } else {
-      // octants: {i, face 1 or 6, sides (m, m+1)}
+      // octants: {i, face 1 or 6, sides (m, m+1)}.  READING (prisms): the
+      // two octants at the collapsed edge (sides 2-3 and 3-4) both take the
+      // sides 2 and 4 that meet there, so a prism has the six corner
+      // stencils of its vertices, the one at the collapsed edge twice.
       for (int top = 0; top < 2; ++top)
         for (int m = 0; m < 4; ++m) {
           std::vector<int> s;
+          int s1 = 1 + m, s2 = 1 + (m + 1) % 4;
+          if (cl.prism && (m == 1 || m == 2)) { s1 = 2; s2 = 4; }
           s.push_back(idx(cl.nb[top ? 5 : 0]));
-          s.push_back(idx(cl.nb[1 + m]));
-          s.push_back(idx(cl.nb[1 + (m + 1) % 4]));
+          s.push_back(idx(cl.nb[s1]));
+          s.push_back(idx(cl.nb[s2]));
           cl.sub.push_back(s);
         }
     }
@@ -1159,6 +1190,7 @@ static void stage_operator(Solver& S, double dt, std::vector<double>& L, std::ve
     for (int v = 0; v < 5; ++v) {
       double s = 0.0, d = 0.0;
       for (int p = 0; p < nfc; ++p) {
+        if (cl.face[p] < 0) continue;
         s += cl.side[p] * FF[cl.face[p] * 5 + v];
         d += cl.side[p] * FD[cl.face[p] * 5 + v];
       }

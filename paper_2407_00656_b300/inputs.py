@@ -11,7 +11,12 @@ Workloads (Section 5 of the paper):
     N^3 lattice split into 6 tetrahedra (Section 5.1), optionally with seeded
     jitter of the interior nodes;
   * flow past a unit-diameter sphere on a six-block hexahedral shell
-    (Section 5.2), with geometric radial growth from the wall.
+    (Section 5.2), with geometric radial growth from the wall, optionally
+    with a seeded share of its columns cut into triangular prisms;
+  * the density wave on the periodic cube cut into triangular prisms.
+
+A triangular prism is passed as a hexahedron whose nodes 2 and 3 coincide and
+whose nodes 6 and 7 coincide: bottom triangle 0 1 2, top triangle 4 5 6.
 """
 from __future__ import annotations
 
@@ -74,6 +79,60 @@ def kuhn_cube(n: int, length: float = 2.0, jitter: float = 0.0, seed: int = 0):
     return xyz, cells, periods
 
 
+def prism_cube(n: int, length: float = 2.0, jitter: float = 0.0, seed: int = 0):
+    """Return (xyz, cells[2 n^3, 8], periods[3]): the periodic cube of
+    ``kuhn_cube`` with every lattice cube cut by the vertical plane through
+    its (0,0)-(1,1) diagonal into two triangular prisms, given as
+    hexahedra with nodes 2 = 3 and 6 = 7 (bottom triangle 0 1 2, top
+    triangle 4 5 6 one lattice step up in z).  Same node jitter as
+    ``kuhn_cube``."""
+    h = length / n
+    m = n + 1
+    ii, jj, kk = np.meshgrid(np.arange(m), np.arange(m), np.arange(m), indexing="ij")
+    xyz = np.stack([ii, jj, kk], axis=-1).reshape(-1, 3).astype(np.float64) * h
+    if jitter > 0.0:
+        rng = np.random.default_rng(seed)
+        off = rng.uniform(-jitter * h, jitter * h, size=xyz.shape)
+        interior = np.all((xyz > 0.5 * h) & (xyz < length - 0.5 * h), axis=1)
+        xyz[interior] += off[interior]
+
+    def nid(i, j, k):
+        return (i * m + j) * m + k
+
+    ci, cj, ck = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    ci, cj, ck = ci.ravel(), cj.ravel(), ck.ravel()
+    b = [nid(ci, cj, ck), nid(ci + 1, cj, ck), nid(ci + 1, cj + 1, ck), nid(ci, cj + 1, ck)]
+    t = [nid(ci, cj, ck + 1), nid(ci + 1, cj, ck + 1), nid(ci + 1, cj + 1, ck + 1), nid(ci, cj + 1, ck + 1)]
+    a_ = np.stack([b[0], b[1], b[2], b[2], t[0], t[1], t[2], t[2]], axis=1)
+    b_ = np.stack([b[0], b[2], b[3], b[3], t[0], t[2], t[3], t[3]], axis=1)
+    cells = np.stack([a_, b_], axis=1).reshape(-1, 8).astype(np.int64)
+    periods = np.array([length, length, length], dtype=np.float64)
+    return xyz, cells, periods
+
+
+def prism_tets(cells: np.ndarray) -> np.ndarray:
+    """The three tetrahedra [n, 3, 4] that make up each prism (nodes
+    2 = 3, 6 = 7) with planar side faces: (0 1 2 4), (1 2 4 5), (2 4 5 6)."""
+    c = np.asarray(cells)
+    return np.stack([c[:, [0, 1, 2, 4]], c[:, [1, 2, 4, 5]], c[:, [2, 4, 5, 6]]], axis=1)
+
+
+def cell_average_sin(xyz: np.ndarray, cells: np.ndarray, t: float) -> np.ndarray:
+    """Exact average of sin(pi (x+y+z-t)) over tetrahedra, or over prisms
+    (hexahedra with nodes 2 = 3, 6 = 7) whose side faces are planar, as the
+    volume-weighted mean over their three tetrahedra."""
+    cells = np.asarray(cells)
+    if cells.shape[1] == 4:
+        return tet_average_sin(xyz, cells, t)
+    if not np.all((cells[:, 2] == cells[:, 3]) & (cells[:, 6] == cells[:, 7])):
+        raise ValueError("exact averages are for tetrahedra and prisms only")
+    tets = prism_tets(cells).reshape(-1, 4)
+    p = xyz[tets]
+    vol = np.abs(np.einsum("ij,ij->i", np.cross(p[:, 1] - p[:, 0], p[:, 2] - p[:, 0]), p[:, 3] - p[:, 0]))
+    avg = tet_average_sin(xyz, tets, t)
+    return (vol * avg).reshape(-1, 3).sum(axis=1) / vol.reshape(-1, 3).sum(axis=1)
+
+
 def _complete_homogeneous(d: np.ndarray, mmax: int) -> np.ndarray:
     """h_m(d_0..d_{k-1}) for m = 0..mmax, per row of d (shape [n,k])."""
     n, k = d.shape
@@ -117,7 +176,7 @@ def density_wave_state(xyz, cells, t: float = 0.0, gamma: float = 1.4, amp: floa
     periods for both.)  Every conservative variable is affine in rho:
     (rho, rho, rho, rho, p/(gamma-1) + 3 rho/2).
     """
-    rho = 1.0 + amp * tet_average_sin(xyz, cells, 3.0 * t)
+    rho = 1.0 + amp * cell_average_sin(xyz, cells, 3.0 * t)
     q = np.empty((len(rho), 5))
     q[:, 0] = rho
     q[:, 1] = rho
@@ -173,8 +232,8 @@ def random_smooth_state(xyz, cells, seed: int = 0, gamma: float = 1.4, amp: floa
 # Six-block hexahedral shell around a sphere (Section 5.2 meshes)
 # ----------------------------------------------------------------------------
 def sphere_shell(n: int, n_r: int, r_wall: float = 0.5, r_far: float = 20.0,
-                 growth: float = 1.08, jitter: float = 0.0, seed: int = 0):
-    """Return (xyz, cells[6 n^2 n_r, 8], bface_nodes[.,4], bface_tag[.]).
+                 growth: float = 1.08, jitter: float = 0.0, seed: int = 0, prism_frac: float = 0.0):
+    """Return (xyz, cells[., 8], bface_nodes[.,4], bface_tag[.]).
 
     The sphere surface is covered by the six faces of a cube, each an n x n
     grid mapped equiangularly onto the sphere; n_r layers of hexahedra grow
@@ -183,6 +242,13 @@ def sphere_shell(n: int, n_r: int, r_wall: float = 0.5, r_far: float = 20.0,
     it, oriented for a positive volume.  Inner faces are tagged as no-slip
     walls, outer faces as far field.  ``jitter`` moves the surface directions
     tangentially by a seeded fraction of the angular spacing.
+
+    With ``prism_frac > 0`` each surface quad is, with that probability
+    (seeded), cut along a diagonal into two triangles, and its column of
+    hexahedra becomes two columns of triangular prisms (hexahedra with nodes
+    2 = 3 and 6 = 7): a hybrid hex/prism shell whose faces all match, since
+    a column's side faces are radial quads either way.  Cells are ordered by
+    layer, then by column; a cut quad's two prisms are adjacent.
     """
     g = growth
     k = np.arange(n_r + 1, dtype=np.float64)
@@ -218,6 +284,16 @@ def sphere_shell(n: int, n_r: int, r_wall: float = 0.5, r_far: float = 20.0,
                     quads.append(pts)
     dirs = np.array(dirs)
     quads = np.array(quads, dtype=np.int64)
+    if prism_frac > 0.0:
+        cut = np.random.default_rng([seed, 7]).random(len(quads)) < prism_frac
+        cols = []
+        for qd, c in zip(quads, cut):
+            if c:
+                cols.append([qd[0], qd[1], qd[2], qd[2]])
+                cols.append([qd[0], qd[2], qd[3], qd[3]])
+            else:
+                cols.append(list(qd))
+        quads = np.array(cols, dtype=np.int64)
     ns = len(dirs)
     if jitter > 0.0:
         rng = np.random.default_rng(seed)
@@ -235,10 +311,14 @@ def sphere_shell(n: int, n_r: int, r_wall: float = 0.5, r_far: float = 20.0,
     nq = np.cross(p[:, 2] - p[:, 0], p[:, 3] - p[:, 1])
     up = p[:, 4:].mean(axis=1) - p[:, :4].mean(axis=1)
     flip = np.einsum("ij,ij->i", nq, up) < 0
-    cells[flip] = cells[flip][:, [0, 3, 2, 1, 4, 7, 6, 5]]
+    prism = cells[:, 2] == cells[:, 3]
+    cells[flip & ~prism] = cells[flip & ~prism][:, [0, 3, 2, 1, 4, 7, 6, 5]]
+    cells[flip & prism] = cells[flip & prism][:, [1, 0, 2, 3, 5, 4, 6, 7]]  # keeps 2 = 3, 6 = 7
     nq_cells = len(quads)
-    wall = cells[:nq_cells, :4]
-    far = cells[-nq_cells:, 4:]
+    wall = cells[:nq_cells, :4].copy()
+    far = cells[-nq_cells:, 4:].copy()
+    wall[prism[:nq_cells], 3] = -1  # triangles, padded
+    far[prism[-nq_cells:], 3] = -1
     bface_nodes = np.concatenate([wall, far], axis=0).astype(np.int64)
     bface_tag = np.concatenate([np.full(nq_cells, BC_WALL), np.full(nq_cells, BC_FARFIELD)]).astype(np.int32)
     return xyz, cells.astype(np.int64), bface_nodes, bface_tag
