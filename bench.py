@@ -7,12 +7,16 @@ mesh.  Metric: cell-updates/s = cells x steps / device time.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hgks|reference]
                     [--precision fp64|mixed]
-                    [--workload densityN | densityNv | sphere | sphereN | transonic | transonicN]
+                    [--workload densityN | densityNv | sphere | sphereN | transonic | transonicN
+                                | hybrid | hybridN | prismN]
                     [--no-cpu-baseline] [--no-serve] [--serve]
 
 densityN: N^3 x 6 tets (densityNv with mu = 1e-3, Pr = 0.72); sphere: the
 1.51M-cell hex shell at Ma 0.2535, Re 300; sphereN: a 6 x N^2 x 1.3N shell;
-transonic, transonicN: the same shells at Ma 1.5, Re 300.
+transonic, transonicN: the same shells at Ma 1.5, Re 300; hybrid: the
+1.46M-cell hex/prism shell 6 x 50^2 x 75 with 30% of its columns cut into
+prisms, Ma 0.2535, Re 300; hybridN: 6 x N^2 x 1.3N likewise; prismN: the
+density wave on N^3 x 2 jittered prisms.
 
 Prints one JSON line (rank 0).  For N > 1 (torchrun) every rank advances its
 own replica of the workload: the path has no exchange step on one GPU per
@@ -81,6 +85,26 @@ def workload(name: str):
         return dict(xyz=xyz, cells=cells, periods=per, q=q, params=params,
                     desc=f"density wave, {n}^3 x 6 tets" + (", jitter 0.15h seed 0" if jit else "") +
                     (", mu 1e-3 Pr 0.72" if visc else ", inviscid"))
+    # prismN: the density wave on N^3 x 2 prisms, jittered, inviscid
+    if name.startswith("prism") and name[len("prism"):].isdigit():
+        n = int(name[len("prism"):])
+        xyz, cells, per = I.prism_cube(n, jitter=0.15, seed=0)
+        q = I.random_smooth_state(xyz, cells, seed=0)
+        return dict(xyz=xyz, cells=cells, periods=per, q=q, params={},
+                    desc=f"smooth state, {n}^3 x 2 prisms, jitter 0.15h seed 0, inviscid")
+    # hybrid: the hex/prism shell of ~1.5M cells (30% of the columns cut into
+    # prisms), Ma 0.2535, Re 300; hybridN: 6 x N^2 x round(1.3 N) columns
+    if name == "hybrid" or (name.startswith("hybrid") and name[len("hybrid"):].isdigit()):
+        size = name[len("hybrid"):]
+        n, nr = (50, 75) if size == "" else (int(size), max(2, round(1.3 * int(size))))
+        xyz, cells, bfn, bft = I.sphere_shell(n, nr, seed=0, prism_frac=0.3)
+        qinf = I.free_stream(0.2535)
+        q = np.tile(qinf, (len(cells), 1))
+        return dict(xyz=xyz, cells=cells, periods=None, bfn=bfn, bft=bft, q=q,
+                    params=dict(q_inf=qinf, mu_ref=0.2535 / 300, Pr=0.72, visc_exp=0.7, T_ref=1 / 1.4,
+                                tau_num_c=1.0),
+                    desc=f"hex/prism shell 6x{n}^2x{nr} columns, 30% cut into prisms, Ma 0.2535 Re 300, "
+                         "wall + far field")
     # sphere: the 1.51M-cell shell 6 x 58^2 x 75 at Ma 0.2535, Re 300;
     # sphereN: 6 x N^2 x round(1.3 N); transonic, transonicN: the same shells
     # at Ma 1.5, Re 300 (the transonic sphere of Section 5.2)
@@ -183,7 +207,8 @@ def run_reference(args, rank, world):
     """The CPU oracle as it stands on the host cores (rank 0 only).  Each
     timed step is one S2O4 step of a bounded sample of the workload: the
     24^3 x 6 jittered mesh for the density-wave workloads, the 6 x 24^2 x 31
-    shell at the workload's Mach number for the sphere workloads."""
+    shell at the workload's Mach number for the sphere workloads, the 6 x 20^2
+    x 26 hybrid shell and the 24^3 x 2 prism cube for those workloads."""
     if rank != 0:
         return
     import oracle
@@ -196,6 +221,10 @@ def run_reference(args, rank, world):
         ws = workload("sphere24")
     elif args.workload.startswith("transonic"):
         ws = workload("transonic24")
+    elif args.workload.startswith("hybrid"):
+        ws = workload("hybrid20")
+    elif args.workload.startswith("prism"):
+        ws = workload("prism24")
     cores = os.cpu_count() or 1
     oracle.set_threads(cores)
     o = oracle.Oracle(ws["xyz"], ws["cells"], ws["periods"], ws.get("bfn"), ws.get("bft"),

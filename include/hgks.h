@@ -53,6 +53,15 @@ enum { HGKS_FP64 = 0, HGKS_FP32_MIXED = 1 };
  *               face opposite node p.  Hex: nodes 0-3 one quad, 4-7 the
  *               opposite quad in the same order; local faces (0,1,2,3),
  *               (0,1,5,4), (1,2,6,5), (2,3,7,6), (3,0,4,7), (4,5,6,7).
+ *               A triangular prism is a hex with nodes 2 = 3 and 6 = 7
+ *               (bottom triangle 0 1 2, top triangle 4 5 6): its face
+ *               (2,3,7,6) collapses to an edge and is dropped, so hex and
+ *               prism cells mix freely in one HGKS_HEX8 mesh.  Any other
+ *               repeated node fails with HGKS_EINVAL.  (The paper defines
+ *               tetrahedra and hexahedra; the prism's faces and sub-stencils
+ *               are this library's reading: triangles take the 3-point rule,
+ *               and the two octant sub-stencils at the collapsed edge both
+ *               take the two side faces meeting there.)
  *   bface_nodes [n_bfaces][4] nodes of tagged boundary faces (-1 pads a
  *               triangle), bface_tag[n_bfaces] one of HGKS_BC_*.
  *   periods     [3] translation lengths along x, y, z used to pair untagged

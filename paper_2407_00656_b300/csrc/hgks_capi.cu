@@ -420,7 +420,10 @@ int make_solver(hgks_dmesh* d, const hgks_params* params, const double* const* q
   w.R = cv.take<double>(5 * m.nc);
   w.Qf = f32 ? cv.take<float>(8 * dm.nce) : nullptr;
   w.coef = cv.take<char>(rs * (f32 ? hgks::kCoefRec32 : hgks::kCoefRec64) * m.nc);
-  w.Fs = cv.take<char>(rs * (f32 ? hgks::kFluxRec32 : hgks::kFluxRec64) * m.nf);
+  // face records, plus one past the last face that no kernel writes: the
+  // cell-face entry of a prism's collapsed side points at it
+  const int64_t frec = rs * (f32 ? hgks::kFluxRec32 : hgks::kFluxRec64);
+  w.Fs = cv.take<char>(frec * (m.nf + 1));
   w.ctl = cv.take<hgks::Control>(n);
   w.bar = cv.take<hgks::GridBar>(1);
   if (cv.off > bytes) { g_err = "internal error: solver arena too small"; return bail(HGKS_ENOMEM); }
@@ -460,6 +463,7 @@ int make_solver(hgks_dmesh* d, const hgks_params* params, const double* const* q
   }
   for (int i = 0; i < n; ++i) to_internal(d->members[i], q0[i], s->hbuf, dm.nce);
   cudaError_t e = cudaMemsetAsync(w.Qs, 0, sizeof(double) * 5 * dm.nce, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(static_cast<char*>(w.Fs) + frec * dm.nf, 0, frec, s->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(w.Q, s->hbuf.data(), sizeof(double) * 5 * dm.nce, cudaMemcpyHostToDevice, s->stream);
   if (e != cudaSuccess) { cuda_fail(e, "copying the initial state"); return bail(HGKS_ECUDA); }

@@ -1821,6 +1821,7 @@ cudaError_t persist_any(const DevMesh& m, const DevParams& p, const DevWork& w, 
     case 20: return persist_launch<Real, 20, 8, 3, 4, 6>(m, p, w, n, s, prep);
     case 22: return persist_launch<Real, 22, 8, 3, 4, 6>(m, p, w, n, s, prep);
     case 24: return persist_launch<Real, 24, 8, 3, 4, 6>(m, p, w, n, s, prep);
+    case 26: return persist_launch<Real, 26, 8, 3, 4, 6>(m, p, w, n, s, prep);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1880,6 +1881,7 @@ void recon_hex(const DevMesh& m, const DevParams& p, const QT* Q, Real* coef, Co
     case 20: recon_launch<Real, QT, 20, 8, 3>(m, p, Q, coef, ctl, s, prep); break;
     case 22: recon_launch<Real, QT, 22, 8, 3>(m, p, Q, coef, ctl, s, prep); break;
     case 24: recon_launch<Real, QT, 24, 8, 3>(m, p, Q, coef, ctl, s, prep); break;
+    case 26: recon_launch<Real, QT, 26, 8, 3>(m, p, Q, coef, ctl, s, prep); break;
     default: break;
   }
 }
@@ -1888,7 +1890,8 @@ void recon_hex(const DevMesh& m, const DevParams& p, const QT* Q, Real* coef, Co
 }  // namespace
 bool stencil_supported(int nfc, int K) {
   if (nfc == 4) return K >= 12 && K <= 16;
-  return K == 18 || K == 20 || K == 22 || K == 24;
+  // hexahedra 18-24; hybrid hex/prism meshes reach 26
+  return K == 18 || K == 20 || K == 22 || K == 24 || K == 26;
 }
 namespace {
 

@@ -10,6 +10,12 @@
 //     boundary condition"),
 //   * the two-layer WENO stencil of Algorithm 1 and the sub-stencils of
 //     Section 2.3 (tetrahedra: four 7-cell stencils; hexahedra: eight octants),
+//   * triangular prisms, given as hexahedra with nodes 2 = 3 and 6 = 7 (the
+//     paper defines no prism): the side face 2 3 7 6 collapses to an edge and
+//     is dropped (its cell-face entry points at a flux record that stays
+//     zero), the two triangles take the 3-point rule padded with a
+//     zero-weight fourth point, and the two octants at the collapsed edge
+//     take the two side faces that meet there,
 //   * least-squares pseudo-inverses for the quadratic P0 and linear Pm of
 //     Eq. polys in coordinates centred on the cell and scaled by |cell|^(1/3),
 //   * face Gauss points: 3-point degree-2 rule on triangles, 2x2 Gauss on
@@ -229,6 +235,25 @@ int build_host_mesh(const hgks_mesh_desc& d, HostMesh& m, std::string& err) {
   auto node = [&](int64_t i) { return P3{d.xyz[3 * i], d.xyz[3 * i + 1], d.xyz[3 * i + 2]}; };
   for (int64_t i = 0; i < nc * ct; ++i)
     if (d.cell_nodes[i] < 0 || d.cell_nodes[i] >= d.n_nodes) { err = "cell node index out of range"; return HGKS_EINVAL; }
+  // prisms: hexahedra with nodes 2 = 3 and 6 = 7 and six distinct nodes
+  std::vector<uint8_t> prism0(nc, 0);
+  if (ct == HGKS_HEX8)
+    for (int64_t c = 0; c < nc; ++c) {
+      const int64_t* v = d.cell_nodes + 8 * c;
+      int distinct = 0;
+      for (int a = 0; a < 8; ++a) {
+        bool seen = false;
+        for (int b = 0; b < a; ++b) seen = seen || v[b] == v[a];
+        distinct += !seen;
+      }
+      prism0[c] = v[2] == v[3] && v[6] == v[7];
+      if (distinct != (prism0[c] ? 6 : 8)) {
+        std::snprintf(buf, sizeof buf, "cell %lld: a hexahedron needs 8 distinct nodes, a prism nodes 2 = 3 and 6 = 7",
+                      (long long)c);
+        err = buf;
+        return HGKS_EINVAL;
+      }
+    }
 
   // ---- 1. cell geometry in caller order
   std::vector<double> vol0(nc), cen0(3 * nc), mom0(6 * nc);
@@ -277,6 +302,22 @@ int build_host_mesh(const hgks_mesh_desc& d, HostMesh& m, std::string& err) {
   for (int64_t i = 0; i < nc; ++i) inv[perm[i]] = (int32_t)i;
   auto cnode = [&](int64_t cnew, int a) { return d.cell_nodes[perm[cnew] * ct + a]; };
   auto lnode = [&](int64_t cnew, int p, int a) { return cnode(cnew, ct == HGKS_TET4 ? kTetFace[p][a] : kHexFace[p][a]); };
+  auto is_prism = [&](int64_t cnew) { return prism0[perm[cnew]] != 0; };
+  // distinct nodes of local face p in cyclic order: fnn, 3 for a prism's
+  // triangles, 0 for its collapsed side face
+  auto face_nodes = [&](int64_t cnew, int p, int64_t out[4]) {
+    if (!is_prism(cnew)) {
+      for (int a = 0; a < fnn; ++a) out[a] = lnode(cnew, p, a);
+      return fnn;
+    }
+    if (p == 3) return 0;
+    if (p == 0 || p == 5) {
+      for (int a = 0; a < 3; ++a) out[a] = lnode(cnew, p, a);
+      return 3;
+    }
+    for (int a = 0; a < 4; ++a) out[a] = lnode(cnew, p, a);
+    return 4;
+  };
   auto ccen = [&](int64_t cnew) { int64_t o = perm[cnew]; return P3{cen0[3 * o], cen0[3 * o + 1], cen0[3 * o + 2]}; };
 
   // ---- 3. faces: sort (cell, local face) incidences by their sorted node keys
@@ -285,14 +326,21 @@ int build_host_mesh(const hgks_mesh_desc& d, HostMesh& m, std::string& err) {
   std::vector<Key> keys(ninc);
   for (int64_t c = 0; c < nc; ++c)
     for (int p = 0; p < nfc; ++p) {
-      Key k = {-1, -1, -1, -1};
-      for (int a = 0; a < fnn; ++a) k[a] = lnode(c, p, a);
-      std::sort(k.begin(), k.begin() + fnn);
+      Key k = {-2, -2, -2, -2};  // a collapsed face: sorts first, never matched
+      int64_t fv[4];
+      const int nn = face_nodes(c, p, fv);
+      if (nn > 0) {
+        k = {-1, -1, -1, -1};
+        for (int a = 0; a < nn; ++a) k[a] = fv[a];
+        std::sort(k.begin(), k.begin() + nn);
+      }
       keys[c * nfc + p] = k;
     }
   std::vector<int64_t> order(ninc);
   std::iota(order.begin(), order.end(), 0);
   std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return keys[a] < keys[b] || (keys[a] == keys[b] && a < b); });
+  int64_t first = 0;  // skip the collapsed faces
+  while (first < ninc && keys[order[first]][0] == -2) ++first;
 
   struct FaceT {
     int32_t own, nbr;   // nbr = -1 for physical boundary
@@ -303,7 +351,7 @@ int build_host_mesh(const hgks_mesh_desc& d, HostMesh& m, std::string& err) {
   std::vector<FaceT> faces;
   faces.reserve(ninc / 2 + 16);
   std::vector<int64_t> singles;
-  for (int64_t i = 0; i < ninc;) {
+  for (int64_t i = first; i < ninc;) {
     int64_t j = i + 1;
     while (j < ninc && keys[order[j]] == keys[order[i]]) ++j;
     if (j - i == 2) {
@@ -335,9 +383,11 @@ int build_host_mesh(const hgks_mesh_desc& d, HostMesh& m, std::string& err) {
   auto face_centroid = [&](int64_t inc) {
     int64_t c = inc / nfc;
     int p = (int)(inc % nfc);
+    int64_t fv[4];
+    const int nn = face_nodes(c, p, fv);
     P3 s = {0, 0, 0};
-    for (int a = 0; a < fnn; ++a) s = s + node(lnode(c, p, a));
-    return (1.0 / fnn) * s;
+    for (int a = 0; a < nn; ++a) s = s + node(fv[a]);
+    return (1.0 / nn) * s;
   };
   double pmax = 0.0;
   if (d.periods)
@@ -431,7 +481,7 @@ int build_host_mesh(const hgks_mesh_desc& d, HostMesh& m, std::string& err) {
   m.fdl.assign(G * 3 * nf, 0.0); m.fdr.assign(G * 3 * nf, 0.0);
   m.fn.assign(G * 3 * nf, 0.0); m.fw.assign(G * nf, 0.0);
   m.cface.assign(nfc * nc, -1);
-  std::vector<Member> nb(nc * nfc);
+  std::vector<Member> nb(nc * nfc, Member{-1, {0, 0, 0}});  // id -1: no face (a prism's collapsed side)
   std::vector<double> area(nc, 0.0);
   std::vector<P3> gpt;  // mirror plane points of the ghosts
   int64_t ng = 0;
@@ -443,8 +493,15 @@ int build_host_mesh(const hgks_mesh_desc& d, HostMesh& m, std::string& err) {
   for (int64_t fi = 0; fi < nf; ++fi) {
     const FaceT& f = faces[fi];
     P3 pts[4];
-    for (int a = 0; a < fnn; ++a) pts[a] = node(lnode(f.own, f.lown, a));
-    FaceGeo g = face_geo(pts, fnn);
+    int64_t fv[4];
+    const int nn = face_nodes(f.own, f.lown, fv);
+    for (int a = 0; a < nn; ++a) pts[a] = node(fv[a]);
+    FaceGeo g = face_geo(pts, nn);
+    for (int k = g.ng; k < G; ++k) {  // a triangle among quads: zero-weight points at the centroid
+      g.x[k] = g.centroid;
+      g.n[k] = g.nmean;
+      g.w[k] = 0.0;
+    }
     P3 co = ccen(f.own);
     if (dotp(g.nmean, g.centroid - co) < 0) {
       for (int k = 0; k < g.ng; ++k) g.n[k] = -1.0 * g.n[k];
@@ -487,6 +544,8 @@ int build_host_mesh(const hgks_mesh_desc& d, HostMesh& m, std::string& err) {
       ++gi;
     }
   }
+  for (int64_t c = 0; c < nc; ++c)
+    if (is_prism(c)) m.cface[3 * nc + c] = (int32_t)(2 * nf);  // the zero flux record past the last face
   for (int64_t i = 0; i < nfc * nc; ++i)
     if (m.cface[i] < 0) { err = "internal error: cell face not assigned"; return HGKS_EMESH; }
 
@@ -543,6 +602,7 @@ int build_host_mesh(const hgks_mesh_desc& d, HostMesh& m, std::string& err) {
   auto big_stencil = [&](int64_t c, Member* out) {
     int n = 0;
     auto add = [&](const Member& r) {
+      if (r.id < 0) return;
       if (r.id == c && r.sh[0] == 0 && r.sh[1] == 0 && r.sh[2] == 0) return;
       for (int k = 0; k < n; ++k) if (out[k] == r) return;
       out[n++] = r;
@@ -550,7 +610,7 @@ int build_host_mesh(const hgks_mesh_desc& d, HostMesh& m, std::string& err) {
     for (int p = 0; p < nfc; ++p) add(nb[c * nfc + p]);
     for (int p = 0; p < nfc; ++p) {
       const Member r = nb[c * nfc + p];
-      if (r.id >= nc) continue;  // ghosts have no neighbours
+      if (r.id < 0 || r.id >= nc) continue;  // ghosts have no neighbours
       for (int q = 0; q < nfc; ++q) {
         Member r2 = nb[(int64_t)r.id * nfc + q];
         for (int a = 0; a < 3; ++a) r2.sh[a] = (int8_t)(r2.sh[a] + r.sh[a]);
@@ -565,6 +625,10 @@ int build_host_mesh(const hgks_mesh_desc& d, HostMesh& m, std::string& err) {
     K = std::max(K, big_stencil(c, tmp));
   }
   if (K < 9) { err = "big stencil has fewer than 9 cells"; return HGKS_EMESH; }
+  // hexahedral meshes: the kernels are compiled for even stencil sizes from
+  // 18 (prisms reach odd ones); shorter stencils are padded with the cell
+  // itself and zero weights
+  if (ct == HGKS_HEX8) K = K <= 18 ? 18 : (K + 1) / 2 * 2;
   m.K = K;
   const int M = m.M, KM = m.KM;
   m.sten.assign((int64_t)K * nc, 0);
@@ -581,6 +645,7 @@ int build_host_mesh(const hgks_mesh_desc& d, HostMesh& m, std::string& err) {
     const int n = big_stencil(c, big);
     (void)KCAP;
     auto pos = [&](const Member& r) {
+      if (r.id < 0) return -1;
       for (int k = 0; k < n; ++k) if (big[k] == r) return k;
       return -1;
     };
@@ -609,12 +674,16 @@ int build_host_mesh(const hgks_mesh_desc& d, HostMesh& m, std::string& err) {
         subn[s] = cnt;
       }
     } else {
+      // octant {bottom|top, side s, side s+1}; a prism's two octants at the
+      // collapsed edge (sides 2-3 and 3-4) take the sides 2 and 4 meeting there
+      const bool pr = is_prism(c);
       for (int top = 0; top < 2; ++top)
         for (int s = 0; s < 4; ++s) {
           const int o = top * 4 + s;
+          const bool edge = pr && (s == 1 || s == 2);
           sub[o][0] = pos(nb[c * nfc + (top ? 5 : 0)]);
-          sub[o][1] = pos(nb[c * nfc + 1 + s]);
-          sub[o][2] = pos(nb[c * nfc + 1 + (s + 1) % 4]);
+          sub[o][1] = pos(nb[c * nfc + (edge ? 2 : 1 + s)]);
+          sub[o][2] = pos(nb[c * nfc + (edge ? 4 : 1 + (s + 1) % 4)]);
           subn[o] = 3;
         }
     }
@@ -715,7 +784,11 @@ int build_union(const std::vector<const HostMesh*>& parts, HostMesh& u, std::vec
         for (int k = 0; k < p.K; ++k) u.pinv0[((int64_t)d * K + k) * ncp + uc] = p.pinv0[((int64_t)d * p.K + k) * p.ncp + c];
       for (int r = 0; r < M * KM; ++r) u.subidx[(int64_t)r * ncp + uc] = p.subidx[(int64_t)r * p.ncp + c];
       for (int r = 0; r < M * 3 * KM; ++r) u.pinvm[(int64_t)r * ncp + uc] = p.pinvm[(int64_t)r * p.ncp + c];
-      for (int q = 0; q < nfc; ++q) u.cface[q * nc + uc] = (int32_t)(p.cface[q * p.nc + c] + 2 * fo);
+      for (int q = 0; q < nfc; ++q) {
+        const int32_t e = p.cface[q * p.nc + c];
+        // a member's zero record (past its faces) becomes the union's
+        u.cface[q * nc + uc] = e == (int32_t)(2 * p.nf) ? (int32_t)(2 * nf) : (int32_t)(e + 2 * fo);
+      }
     }
     for (int64_t g = 0; g < p.ng; ++g) {
       u.gsrc[go + g] = (int32_t)(co + p.gsrc[g]);
@@ -765,7 +838,7 @@ int64_t solver_work_bytes(const HostMesh& m, int precision, int nmesh) {
   b += al(8 * 5 * nc);                         // R (partial S2O4 sum)
   if (f32) b += al(4 * 8 * nce);               // binary32 copy of the stage state, 32 B per cell
   b += al(rs * (f32 ? kCoefRec32 : kCoefRec64) * nc);  // reconstruction coefficients
-  b += al(rs * (f32 ? kFluxRec32 : kFluxRec64) * nf);  // face flux and its time slope
+  b += al(rs * (f32 ? kFluxRec32 : kFluxRec64) * (nf + 1));  // face flux and its time slope, + a zero record
   b += al((int64_t)sizeof(Control) * nmesh);  // control blocks
   b += al((int64_t)sizeof(GridBar));           // barrier of the persistent step kernel
   return b + 256;

@@ -41,7 +41,8 @@ struct HostMesh {
   std::vector<double> pinv0;     // [9*K][ncp] quadratic least-squares inverse, row d col k at d*K+k
   std::vector<uint8_t> subidx;   // [M*KM][ncp] positions in the big stencil
   std::vector<double> pinvm;     // [M*3*KM][ncp] linear inverses, (m,d,r) at (m*3+d)*KM+r
-  std::vector<int32_t> cface;    // [nfc][nc] 2*face + (1 if the cell is the face's neighbour)
+  std::vector<int32_t> cface;    // [nfc][nc] 2*face + (1 if the cell is the face's neighbour);
+                                 // 2*nf for the collapsed side of a prism (a flux record kept zero)
 
   // per ghost (one per physical boundary face)
   std::vector<int32_t> gsrc;     // [ng] mirrored interior cell
