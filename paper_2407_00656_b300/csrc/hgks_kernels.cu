@@ -1110,6 +1110,9 @@ __global__ void __launch_bounds__(kRThreads) k_recon(DevMesh m, DevParams P, con
 // The copy loops issue their loads back to back (coalesced rows of 32 cells
 // for the per-cell arrays), so each thread keeps many loads in flight.  The
 // arithmetic and its order are those of k_recon.
+// Where leaving out the own-state and geometry rows lets one more block fit
+// on an SM (the stencil sizes 15 and 26), the layout is "lean": each thread
+// then loads its cell's state, second moments and 1/h into registers.
 template <int K, int M, int KM>
 struct ReconSmemF {
   static constexpr int kRows = 9 * K + M * 3 * KM;
@@ -1118,7 +1121,12 @@ struct ReconSmemF {
   static constexpr size_t own = sizeof(float) * 5 * kRC;       // own states [5][kRC]
   static constexpr size_t geo = sizeof(float) * 7 * kRC;       // mom (6) and 1/h [7][kRC]
   static constexpr size_t sub = (size_t)M * KM * kRC;          // sub-stencil positions
-  static constexpr size_t bytes = tile + nbr + own + geo + sub;
+  static constexpr size_t full = tile + nbr + own + geo + sub;
+  // blocks per SM: 228 KB of shared memory, 1 KB reserved per block
+  static constexpr int fit(size_t b) { return (int)(233472 / (b + 1024)); }
+  // (only where the extra block also fits the registers, at about 64 a thread)
+  static constexpr bool lean = fit(full - own - geo) > fit(full) && fit(full - own - geo) * kRThreads * 64 <= 65536;
+  static constexpr size_t bytes = lean ? full - own - geo : full;
 };
 
 template <int K, int M, int KM, bool COH = false>
@@ -1127,9 +1135,9 @@ __device__ __forceinline__ void recon_rs_block(const DevMesh& m, const DevParams
   using S = ReconSmemF<K, M, KM>;
   float* tile = reinterpret_cast<float*>(smem_raw);                              // [kRows][kRC]
   float* snbr = reinterpret_cast<float*>(smem_raw + S::tile);                    // [5][K][kRC]
-  float* sown = reinterpret_cast<float*>(smem_raw + S::tile + S::nbr);           // [5][kRC]
-  float* sgeo = reinterpret_cast<float*>(smem_raw + S::tile + S::nbr + S::own);  // [7][kRC]
-  uint8_t* ssub = smem_raw + S::tile + S::nbr + S::own + S::geo;                 // [M*KM][kRC]
+  float* sown = reinterpret_cast<float*>(smem_raw + S::tile + S::nbr);           // [5][kRC] (not lean)
+  float* sgeo = reinterpret_cast<float*>(smem_raw + S::tile + S::nbr + S::own);  // [7][kRC] (not lean)
+  uint8_t* ssub = smem_raw + S::tile + S::nbr + (S::lean ? 0 : S::own + S::geo);  // [M*KM][kRC]
   const int64_t nc = m.nc, ncp = m.ncp;
   const int t = threadIdx.x;
   const int nv = nc - c0 < kRC ? (int)(nc - c0) : kRC;  // cells of this block
@@ -1138,8 +1146,10 @@ __device__ __forceinline__ void recon_rs_block(const DevMesh& m, const DevParams
   // advance by a fixed stride.
   const int lane = t & 31, v = t >> 5;
   const bool live = lane < nv;
-  // 1. stencil indices of this thread's neighbour entries (entry K: the cell itself)
-  constexpr int NE = (K + 1 + 4) / 5;
+  // 1. stencil indices of this thread's neighbour entries (entry K: the cell
+  // itself, staged unless lean)
+  constexpr int KE = S::lean ? K : K + 1;
+  constexpr int NE = (KE + 4) / 5;
   int32_t jn[NE];
 #pragma unroll
   for (int i = 0; i < NE; ++i) {
@@ -1164,9 +1174,17 @@ __device__ __forceinline__ void recon_rs_block(const DevMesh& m, const DevParams
   // 3. neighbour and own state records (32 bytes each)
   float4 qa[NE];
   float qb[NE];
+  float qown = 0.f, gl[7];
+  if constexpr (S::lean) {
+    if (live) {
+      qown = ldro<COH>(Qf + 8 * (c0 + lane) + v);
+#pragma unroll
+      for (int r = 0; r < 7; ++r) gl[r] = cvt<float>(r < 6 ? m.mom[(int64_t)r * nc + c0 + lane] : m.hinv[c0 + lane]);
+    }
+  }
 #pragma unroll
   for (int i = 0; i < NE; ++i) {
-    if (v + 5 * i <= K && live) {
+    if (v + 5 * i < KE && live) {
       qa[i] = ldro<COH>(reinterpret_cast<const float4*>(Qf + 8 * (int64_t)jn[i]));
       qb[i] = ldro<COH>(Qf + 8 * (int64_t)jn[i] + 4);
     }
@@ -1217,7 +1235,7 @@ __device__ __forceinline__ void recon_rs_block(const DevMesh& m, const DevParams
 #pragma unroll
   for (int i = 0; i < NE; ++i) {
     const int k = v + 5 * i;
-    if (k <= K && live) {
+    if (k < KE && live) {
       float* dst = k < K ? snbr + k * kRC + lane : sown + lane;
       const int vs = k < K ? K * kRC : kRC;
       dst[0] = qa[i].x;
@@ -1229,12 +1247,13 @@ __device__ __forceinline__ void recon_rs_block(const DevMesh& m, const DevParams
   }
   // 6. sub-stencil positions, second moments and 1/h
   for (int r = v; r < M * KM; r += 5) ssub[r * kRC + lane] = m.subidx[(int64_t)r * ncp + c0 + lane];
-  for (int r = v; r < 7; r += 5)
-    if (live) sgeo[r * kRC + lane] = cvt<float>(r < 6 ? m.mom[(int64_t)r * nc + c0 + lane] : m.hinv[c0 + lane]);
+  if constexpr (!S::lean)
+    for (int r = v; r < 7; r += 5)
+      if (live) sgeo[r * kRC + lane] = cvt<float>(r < 6 ? m.mom[(int64_t)r * nc + c0 + lane] : m.hinv[c0 + lane]);
   __syncthreads();
   float res[10];
   if (live) {
-  const float qv = sown[v * kRC + lane];
+  const float qv = S::lean ? qown : sown[v * kRC + lane];
   float dq[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) dq[k] = snbr[(v * K + k) * kRC + lane] - qv;
@@ -1302,8 +1321,8 @@ __device__ __forceinline__ void recon_rs_block(const DevMesh& m, const DevParams
   }
   float mi[6];
 #pragma unroll
-  for (int q = 0; q < 6; ++q) mi[q] = sgeo[q * kRC + lane];
-  const float hi = sgeo[6 * kRC + lane];
+  for (int q = 0; q < 6; ++q) mi[q] = S::lean ? gl[q] : sgeo[q * kRC + lane];
+  const float hi = S::lean ? gl[6] : sgeo[6 * kRC + lane];
   const float glin = P.f_glin, g0 = 1.f - float(M) * glin, eps = P.f_eps;
   recon_finish<float, M>(a, b, qv, mi, hi, glin, g0, eps, res);
   }
