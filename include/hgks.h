@@ -209,7 +209,9 @@ int hgks_batch_init(hgks_mesh* const* meshes, int n, const hgks_params* params, 
 int hgks_members(const hgks_solver* s);
 
 /* Replace the state with q ([n_cells][5] host, caller order) at time t and
- * reset the step counter (restart / resume).  Synchronises. */
+ * reset the step counter (restart / resume).  Synchronises.  The states are
+ * copied as they are (pinned host memory copies fastest) and put into the
+ * internal cell order on the device; hgks_read does the reverse. */
 int hgks_write(hgks_solver* s, const double* q, double t);
 
 /* hgks_write / hgks_read for one member of a batched solver. */

@@ -54,7 +54,6 @@ struct hgks_solver {
   void* arena = nullptr;  // state and work arrays, stream-ordered on `stream`
   size_t arena_bytes = 0;
   cudaGraphExec_t graph = nullptr;
-  std::vector<double> hbuf;  // host staging in the internal SoA layout
 };
 
 namespace {
@@ -112,13 +111,7 @@ int check_params(const hgks_params* p) {
   return HGKS_OK;
 }
 
-// member's caller order [n][5] -> internal SoA [5][stride] at the member's offset
-void to_internal(const Member& mb, const double* q, std::vector<double>& h, int64_t stride) {
-  for (int64_t c = 0; c < mb.nc; ++c) {
-    const double* s = q + 5 * mb.perm[c];
-    for (int v = 0; v < 5; ++v) h[v * stride + mb.coff + c] = s[v];
-  }
-}
+// internal SoA [5][stride] at the member's offset -> member's caller order [n][5]
 void to_caller(const Member& mb, const double* h, int64_t stride, double* q) {
   for (int64_t c = 0; c < mb.nc; ++c) {
     double* d = q + 5 * mb.perm[c];
@@ -309,7 +302,7 @@ int make_dmesh(const hgks::HostMesh& m, std::vector<Member> members, const std::
   double* p_volinv = cv.take<double>(m.nc);
   double* p_hdt = cv.take<double>(m.nc);
   double* p_hinv = cv.take<double>(m.nc);
-  cv.take<double>(m.nc);      // spare slot kept by the size formula
+  int32_t* p_perm = reinterpret_cast<int32_t*>(cv.take<double>(m.nc));  // caller index of each cell
   cv.take<double>(3 * m.nc);  // centroids are baked into the face offsets; slot kept for the size formula
   double* p_mom = cv.take<double>(6 * m.nc);
   int32_t* p_sten = cv.take<int32_t>((int64_t)m.K * m.nc);
@@ -332,11 +325,22 @@ int make_dmesh(const hgks::HostMesh& m, std::vector<Member> members, const std::
   dm.subidx = p_subidx; dm.pinvm = p_pinvm; dm.cface = p_cface; dm.gsrc = p_gsrc; dm.gtag = p_gtag; dm.gnrm = p_gnrm;
   dm.fown = p_fown; dm.fnbr = p_fnbr; dm.fdl = p_fdl; dm.fdr = p_fdr; dm.fn = p_fn; dm.fw = p_fw;
   dm.cmesh = p_cmesh;
+  dm.perm = p_perm;
+  std::vector<int32_t> perm32;
+  try {
+    perm32.resize(m.nc);
+  } catch (const std::bad_alloc&) {
+    g_err = "host allocation failed";
+    return bail(HGKS_ENOMEM);
+  }
+  for (const Member& mb : d->members)
+    for (int64_t c = 0; c < mb.nc; ++c) perm32[mb.coff + c] = (int32_t)mb.perm[c];
   cudaError_t ue = cudaSuccess;
   auto chk = [&](cudaError_t x) { if (ue == cudaSuccess) ue = x; };
   chk(up(p_volinv, volinv, st));
   chk(up(p_hdt, m.hdt, st));
   chk(up(p_hinv, m.hinv, st));
+  chk(up(p_perm, perm32, st));
   chk(up(p_mom, m.mom, st));
   chk(up(p_sten, m.sten, st));
   chk(up(p_pinv0, m.pinv0, st));
@@ -454,18 +458,17 @@ int make_solver(hgks_dmesh* d, const hgks_params* params, const double* const* q
   }
   dp.recon_variant = 0;
   hgks::prepare_kernels(dm, s->precision);
-  // initial states (the ghost slots and Q* start at zero)
-  try {
-    s->hbuf.assign(5 * dm.nce, 0.0);
-  } catch (const std::bad_alloc&) {
-    g_err = "host allocation failed";
-    return bail(HGKS_ENOMEM);
+  // initial states: each member's caller-order states are copied into Q*
+  // (free until the first step) and permuted into Q on the device; the ghost
+  // slots and Q* then start at zero
+  cudaError_t e = cudaMemsetAsync(w.Q, 0, sizeof(double) * 5 * dm.nce, s->stream);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    const Member& mb = d->members[i];
+    e = cudaMemcpyAsync(w.Qs, q0[i], sizeof(double) * 5 * mb.nc, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) hgks::launch_state_in(dm, w.Qs, mb.coff, mb.nc, w.Q, s->stream);
   }
-  for (int i = 0; i < n; ++i) to_internal(d->members[i], q0[i], s->hbuf, dm.nce);
-  cudaError_t e = cudaMemsetAsync(w.Qs, 0, sizeof(double) * 5 * dm.nce, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.Qs, 0, sizeof(double) * 5 * dm.nce, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(static_cast<char*>(w.Fs) + frec * dm.nf, 0, frec, s->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(w.Q, s->hbuf.data(), sizeof(double) * 5 * dm.nce, cudaMemcpyHostToDevice, s->stream);
   if (e != cudaSuccess) { cuda_fail(e, "copying the initial state"); return bail(HGKS_ECUDA); }
   hgks::launch_reset(dm, dp, w, s->precision, -1, 0.0, s->stream);
   e = cudaStreamSynchronize(s->stream);
@@ -596,13 +599,13 @@ int hgks_members(const hgks_solver* s) { return s ? (int)s->members().size() : -
 int hgks_member_write(hgks_solver* s, int member, const double* q, double t) {
   if (!s || !q) return fail(HGKS_EINVAL, "NULL argument");
   if (member < 0 || member >= (int)s->members().size()) return fail(HGKS_EINVAL, "member out of range");
-  HGKS_CUDA(cudaStreamSynchronize(s->stream), "waiting for queued work");
-  s->hbuf.resize(5 * s->dm.nce);
-  HGKS_CUDA(cudaMemcpy(s->hbuf.data(), s->dw.Q, sizeof(double) * 5 * s->dm.nce, cudaMemcpyDeviceToHost),
-            "reading the state");
-  to_internal(s->members()[member], q, s->hbuf, s->dm.nce);
-  HGKS_CUDA(cudaMemcpyAsync(s->dw.Q, s->hbuf.data(), sizeof(double) * 5 * s->dm.nce, cudaMemcpyHostToDevice, s->stream),
+  // the caller's states go into Q* (scratch between steps; ordered after the
+  // queued steps on the solver's stream) and are permuted into the member's
+  // cells of Q on the device
+  const Member& mb = s->members()[member];
+  HGKS_CUDA(cudaMemcpyAsync(s->dw.Qs, q, sizeof(double) * 5 * mb.nc, cudaMemcpyHostToDevice, s->stream),
             "copying the state");
+  hgks::launch_state_in(s->dm, s->dw.Qs, mb.coff, mb.nc, s->dw.Q, s->stream);
   hgks::launch_reset(s->dm, s->dp, s->dw, s->precision, member, t, s->stream);
   HGKS_CUDA(cudaStreamSynchronize(s->stream), "writing the state");
   HGKS_CUDA(cudaGetLastError(), "writing the state");
@@ -662,13 +665,15 @@ int hgks_sync(hgks_solver* s) {
 int hgks_member_read(hgks_solver* s, int member, double* q_out, double* t_out, int64_t* steps_out) {
   if (!s) return fail(HGKS_EINVAL, "NULL solver");
   if (member < 0 || member >= (int)s->members().size()) return fail(HGKS_EINVAL, "member out of range");
-  HGKS_CUDA(cudaStreamSynchronize(s->stream), "synchronising");
   if (q_out) {
-    s->hbuf.resize(5 * s->dm.nce);
-    HGKS_CUDA(cudaMemcpy(s->hbuf.data(), s->dw.Q, sizeof(double) * 5 * s->dm.nce, cudaMemcpyDeviceToHost),
+    // permuted into the caller's order in Q* (scratch between steps), then copied out
+    const Member& mb = s->members()[member];
+    hgks::launch_state_out(s->dm, s->dw.Q, mb.coff, mb.nc, s->dw.Qs, s->stream);
+    HGKS_CUDA(cudaMemcpyAsync(q_out, s->dw.Qs, sizeof(double) * 5 * mb.nc, cudaMemcpyDeviceToHost, s->stream),
               "reading the state");
-    to_caller(s->members()[member], s->hbuf.data(), s->dm.nce, q_out);
   }
+  HGKS_CUDA(cudaStreamSynchronize(s->stream), "synchronising");
+  HGKS_CUDA(cudaGetLastError(), "reading the state");
   hgks::Control c;
   const int rc = read_flags(s, member, &c);
   if (t_out) *t_out = c.t;

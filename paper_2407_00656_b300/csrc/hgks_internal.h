@@ -15,6 +15,7 @@ struct DevMesh {
   int64_t ncp;              // row pitch of pinv0, subidx, pinvm (nc rounded up to 32)
   int nmesh;                // member meshes of a batch (1 for a single mesh)
   const int32_t* cmesh;     // [nc] member of each cell, or nullptr when nmesh == 1
+  const int32_t* perm;      // [nc] caller index of each cell within its member mesh
   int K, M, KM, G, nfc;
   const double* volinv;   // [nc] 1/|cell|
   const double* hdt;      // [nc]
@@ -145,6 +146,11 @@ void launch_control(const DevMesh& m, const DevWork& w, double t_end, double dt_
 // the binary32 state if needed and compute the step bounds of the state.
 void launch_reset(const DevMesh& m, const DevParams& p, const DevWork& w, int precision, int only, double t,
                   cudaStream_t s);
+// States in the caller's order and layout ([n][5] binary64, member-local
+// cell index) to and from the internal order and layout: cells coff .. coff+n-1
+// of Q ([5][nce]).  `in` and `out` are device buffers.
+void launch_state_in(const DevMesh& m, const double* in, int64_t coff, int64_t n, double* Q, cudaStream_t s);
+void launch_state_out(const DevMesh& m, const double* Q, int64_t coff, int64_t n, double* out, cudaStream_t s);
 // L and dL/dt of the current state for step dt into Qs[0:5] and R (as L) -- test path.
 void launch_operator(const DevMesh& m, const DevParams& p, const DevWork& w, int precision, double dt,
                      double* L, double* dL, cudaStream_t s);

@@ -1654,6 +1654,26 @@ __global__ void __launch_bounds__(kBlock) k_update2(DevMesh m, DevParams P, cons
 }
 
 // Binary32 copy of the state (mixed precision).
+// Caller order and layout ([n][5], member-local index perm[c]) to the internal
+// structure-of-arrays order of cells coff .. coff+n-1, and back.
+__global__ void k_state_in(const double* __restrict__ in, const int32_t* __restrict__ perm, int64_t coff,
+                           int64_t n, double* __restrict__ Q, int64_t nce) {
+  const int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (i >= n) return;
+  const double* src = in + 5 * (int64_t)perm[coff + i];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) Q[v * nce + coff + i] = src[v];
+}
+
+__global__ void k_state_out(const double* __restrict__ Q, const int32_t* __restrict__ perm, int64_t coff,
+                            int64_t n, int64_t nce, double* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (i >= n) return;
+  double* dst = out + 5 * (int64_t)perm[coff + i];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) dst[v] = Q[v * nce + coff + i];
+}
+
 __global__ void k_tofloat(const double* __restrict__ Q, float* __restrict__ Qf, int64_t nce) {
   const int64_t c = (int64_t)blockIdx.x * kBlock + threadIdx.x;
   if (c >= nce) return;
@@ -1978,6 +1998,14 @@ void stage_pair(const DevMesh& m, const DevParams& p, const DevWork& w, bool mix
 
 void launch_setdt(const DevMesh& m, const DevWork& w, double dt, cudaStream_t s) {
   k_setdt<<<(m.nmesh + 127) / 128, 128, 0, s>>>(w.ctl, m.nmesh, dt);
+}
+
+void launch_state_in(const DevMesh& m, const double* in, int64_t coff, int64_t n, double* Q, cudaStream_t s) {
+  if (n > 0) k_state_in<<<blocks(n), kBlock, 0, s>>>(in, m.perm, coff, n, Q, m.nce);
+}
+
+void launch_state_out(const DevMesh& m, const double* Q, int64_t coff, int64_t n, double* out, cudaStream_t s) {
+  if (n > 0) k_state_out<<<blocks(n), kBlock, 0, s>>>(Q, m.perm, coff, n, m.nce, out);
 }
 
 float time_stage(const DevMesh& m, const DevParams& p, const DevWork& w, int precision, int reps, cudaStream_t s) {

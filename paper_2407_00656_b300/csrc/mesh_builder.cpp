@@ -814,7 +814,7 @@ int64_t mesh_static_bytes(const HostMesh& m, int nmesh) {
   auto al = [](int64_t b) { return (b + 255) / 256 * 256; };
   const int64_t nc = m.nc, nf = m.nf, ng = m.ng, ncp = m.ncp;
   int64_t b = 0;
-  b += al(8 * nc) * 4;                         // volinv, hdt, hinv, (spare)
+  b += al(8 * nc) * 4;                         // volinv, hdt, hinv, caller index (int32 in an 8-byte slot)
   b += al(8 * 3 * nc) + al(8 * 6 * nc);        // (centroid slot), mom
   b += al(4 * (int64_t)m.K * nc);              // sten
   b += al(8 * (int64_t)9 * m.K * ncp);         // pinv0
