@@ -1110,23 +1110,40 @@ __global__ void __launch_bounds__(kRThreads) k_recon(DevMesh m, DevParams P, con
 // The copy loops issue their loads back to back (coalesced rows of 32 cells
 // for the per-cell arrays), so each thread keeps many loads in flight.  The
 // arithmetic and its order are those of k_recon.
-// Where leaving out the own-state and geometry rows lets one more block fit
-// on an SM (the stencil sizes 15 and 26), the layout is "lean": each thread
-// then loads its cell's state, second moments and 1/h into registers.
+// Two ways to take less shared memory, used where they let more blocks share
+// an SM (the choice is made at compile time from the sizes):
+//   - "phased": the tile holds the quadratic rows (9K) first; once every
+//     warp has formed its quadratic coefficients, the linear sub-stencil rows
+//     replace them, so the tile needs max(9K, 3 M KM) rows, not the sum;
+//   - "lean": the own-state and geometry rows are left out, and each thread
+//     loads its cell's state, second moments and 1/h into registers.
+// The block count is capped by the registers a thread needs (about 56 on
+// tetrahedra, 66 on hexahedra, 86 at stencil size 26, measured with ptxas),
+// and the kernel's launch bounds ask the compiler for that count.
 template <int K, int M, int KM>
 struct ReconSmemF {
-  static constexpr int kRows = 9 * K + M * 3 * KM;
-  static constexpr size_t tile = sizeof(float) * kRows * kRC;  // binary32 rows
-  static constexpr size_t nbr = sizeof(float) * 5 * K * kRC;   // neighbour states [5][K][kRC]
-  static constexpr size_t own = sizeof(float) * 5 * kRC;       // own states [5][kRC]
-  static constexpr size_t geo = sizeof(float) * 7 * kRC;       // mom (6) and 1/h [7][kRC]
-  static constexpr size_t sub = (size_t)M * KM * kRC;          // sub-stencil positions
-  static constexpr size_t full = tile + nbr + own + geo + sub;
-  // blocks per SM: 228 KB of shared memory, 1 KB reserved per block
+  static constexpr int R0 = 9 * K, R1 = M * 3 * KM;  // quadratic and linear rows
+  static constexpr size_t nbr = sizeof(float) * 5 * K * kRC;  // neighbour states [5][K][kRC]
+  static constexpr size_t own = sizeof(float) * 5 * kRC;      // own states [5][kRC]
+  static constexpr size_t geo = sizeof(float) * 7 * kRC;      // mom (6) and 1/h [7][kRC]
+  static constexpr size_t sub = (size_t)M * KM * kRC;         // sub-stencil positions
+  static constexpr size_t rows_f = sizeof(float) * (R0 + R1) * kRC, rows_p = sizeof(float) * (R0 > R1 ? R0 : R1) * kRC;
+  // blocks per SM: 228 KB of shared memory, 1 KB reserved per block; registers
   static constexpr int fit(size_t b) { return (int)(233472 / (b + 1024)); }
-  // (only where the extra block also fits the registers, at about 64 a thread)
-  static constexpr bool lean = fit(full - own - geo) > fit(full) && fit(full - own - geo) * kRThreads * 64 <= 65536;
-  static constexpr size_t bytes = lean ? full - own - geo : full;
+  static constexpr int reg_cap = 65536 / (kRThreads * (M == 4 ? 56 : (K <= 24 ? 66 : 86)));
+  static constexpr int cap(int b) { return b < reg_cap ? b : reg_cap; }
+  static constexpr int b_full = cap(fit(rows_f + nbr + own + geo + sub)), b_lean = cap(fit(rows_f + nbr + sub)),
+                       b_ph = cap(fit(rows_p + nbr + own + geo + sub)), b_phl = cap(fit(rows_p + nbr + sub));
+  static constexpr int best = b_full > b_lean ? (b_full > b_ph ? (b_full > b_phl ? b_full : b_phl)
+                                                               : (b_ph > b_phl ? b_ph : b_phl))
+                                              : (b_lean > b_ph ? (b_lean > b_phl ? b_lean : b_phl)
+                                                               : (b_ph > b_phl ? b_ph : b_phl));
+  // the simplest layout that reaches the best count
+  static constexpr bool phased = b_full < best && b_lean < best;
+  static constexpr bool lean = phased ? b_ph < best : b_full < best;
+  static constexpr size_t tile = phased ? rows_p : rows_f;  // binary32 rows
+  static constexpr size_t bytes = tile + nbr + (lean ? 0 : own + geo) + sub;
+  static constexpr int blocks = best;
 };
 
 template <int K, int M, int KM, bool COH = false>
@@ -1211,10 +1228,12 @@ __device__ __forceinline__ void recon_rs_block(const DevMesh& m, const DevParams
     for (int i = 0; i < REM0; ++i) d[i * RS] = cvt<float>(pv[i]);
     if (v < T0) tile[(5 * J0 + v) * kRC + lane] = cvt<float>(__ldcs(p0 + J0 * step));
   }
-  {
+  // linear sub-stencil rows, at tile row R0 (after the quadratic rows) or,
+  // phased, at row 0 once the quadratic coefficients are formed
+  auto stage_linear = [&](float* dbase) {
     const double* p1 = m.pinvm + (int64_t)v * ncp + c0 + lane;
     const double* q = p1;
-    float* d = d0 + R0 * kRC;
+    float* d = dbase;
 #pragma unroll 1
     for (int j = 0; j + B <= J1; j += B) {
 #pragma unroll
@@ -1229,8 +1248,9 @@ __device__ __forceinline__ void recon_rs_block(const DevMesh& m, const DevParams
     for (int i = 0; i < REM1; ++i) pv[i] = __ldcs(q + i * step);
 #pragma unroll
     for (int i = 0; i < REM1; ++i) d[i * RS] = cvt<float>(pv[i]);
-    if (v < T1) tile[(R0 + 5 * J1 + v) * kRC + lane] = cvt<float>(__ldcs(p1 + J1 * step));
-  }
+    if (v < T1) dbase[J1 * RS] = cvt<float>(__ldcs(p1 + J1 * step));
+  };
+  if constexpr (!S::phased) stage_linear(d0 + R0 * kRC);
   // 5. neighbour states to shared memory ([5][K][kRC]; own states [5][kRC])
 #pragma unroll
   for (int i = 0; i < NE; ++i) {
@@ -1252,85 +1272,92 @@ __device__ __forceinline__ void recon_rs_block(const DevMesh& m, const DevParams
       if (live) sgeo[r * kRC + lane] = cvt<float>(r < 6 ? m.mom[(int64_t)r * nc + c0 + lane] : m.hinv[c0 + lane]);
   __syncthreads();
   float res[10];
-  if (live) {
-  const float qv = S::lean ? qown : sown[v * kRC + lane];
-  float dq[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) dq[k] = snbr[(v * K + k) * kRC + lane] - qv;
-  auto row = [&](int r) -> float { return tile[r * kRC + lane]; };
   // least-squares polynomials (the operation order of k_recon).  On
   // hexahedra, pairs of output rows advance together in packed binary32 FMAs
   // (two independent round-to-nearest FMAs per instruction: the same
   // results); measured 8% faster there and 5% slower on tetrahedra.
+  auto row = [&](int r) -> float { return tile[r * kRC + lane]; };
+  constexpr int LB = S::phased ? 0 : R0;  // tile row of the first linear row
   float a[9];
   float b[M][3];
-  if constexpr (M == 8) {
-    float2 dq2[K];
+  float qv = 0.f;
+  if (live) {
+    qv = S::lean ? qown : sown[v * kRC + lane];
+    float dq[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) dq2[k] = make_float2(dq[k], dq[k]);
+    for (int k = 0; k < K; ++k) dq[k] = snbr[(v * K + k) * kRC + lane] - qv;
+    if constexpr (M == 8) {
+      float2 dq2[K];
 #pragma unroll
-    for (int d = 0; d < 8; d += 2) {
-      float2 acc = make_float2(0.f, 0.f);
+      for (int k = 0; k < K; ++k) dq2[k] = make_float2(dq[k], dq[k]);
 #pragma unroll
-      for (int k = 0; k < K; ++k) acc = __ffma2_rn(make_float2(row(d * K + k), row((d + 1) * K + k)), dq2[k], acc);
-      a[d] = acc.x;
-      a[d + 1] = acc.y;
-    }
-    float sacc = 0.f;
+      for (int d = 0; d < 8; d += 2) {
+        float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int k = 0; k < K; ++k) sacc = fmaf(row(8 * K + k), dq[k], sacc);
-    a[8] = sacc;
-#pragma unroll
-    for (int s = 0; s < M; ++s) {
-      float x[KM];
-#pragma unroll
-      for (int r = 0; r < KM; ++r) x[r] = snbr[(v * K + ssub[(s * KM + r) * kRC + lane]) * kRC + lane] - qv;
-      float2 acc = make_float2(0.f, 0.f);
-      float acc2 = 0.f;
-#pragma unroll
-      for (int r = 0; r < KM; ++r) {
-        acc = __ffma2_rn(make_float2(row(9 * K + (s * 3) * KM + r), row(9 * K + (s * 3 + 1) * KM + r)),
-                         make_float2(x[r], x[r]), acc);
-        acc2 = fmaf(row(9 * K + (s * 3 + 2) * KM + r), x[r], acc2);
+        for (int k = 0; k < K; ++k) acc = __ffma2_rn(make_float2(row(d * K + k), row((d + 1) * K + k)), dq2[k], acc);
+        a[d] = acc.x;
+        a[d + 1] = acc.y;
       }
-      b[s][0] = acc.x;
-      b[s][1] = acc.y;
-      b[s][2] = acc2;
-    }
-  } else {
-#pragma unroll
-    for (int d = 0; d < 9; ++d) {
       float sacc = 0.f;
 #pragma unroll
-      for (int k = 0; k < K; ++k) sacc += row(d * K + k) * dq[k];
-      a[d] = sacc;
-    }
+      for (int k = 0; k < K; ++k) sacc = fmaf(row(8 * K + k), dq[k], sacc);
+      a[8] = sacc;
+    } else {
 #pragma unroll
-    for (int s = 0; s < M; ++s) {
-      float x[KM];
+      for (int d = 0; d < 9; ++d) {
+        float sacc = 0.f;
 #pragma unroll
-      for (int r = 0; r < KM; ++r) x[r] = snbr[(v * K + ssub[(s * KM + r) * kRC + lane]) * kRC + lane] - qv;
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        float acc = 0.f;
-#pragma unroll
-        for (int r = 0; r < KM; ++r) acc += row(9 * K + (s * 3 + d) * KM + r) * x[r];
-        b[s][d] = acc;
+        for (int k = 0; k < K; ++k) sacc += row(d * K + k) * dq[k];
+        a[d] = sacc;
       }
     }
   }
-  float mi[6];
+  if constexpr (S::phased) {
+    __syncthreads();  // every warp has read its quadratic rows
+    stage_linear(d0);
+    __syncthreads();
+  }
+  if (live) {
 #pragma unroll
-  for (int q = 0; q < 6; ++q) mi[q] = S::lean ? gl[q] : sgeo[q * kRC + lane];
-  const float hi = S::lean ? gl[6] : sgeo[6 * kRC + lane];
-  const float glin = P.f_glin, g0 = 1.f - float(M) * glin, eps = P.f_eps;
-  recon_finish<float, M>(a, b, qv, mi, hi, glin, g0, eps, res);
+    for (int s = 0; s < M; ++s) {
+      float x[KM];
+#pragma unroll
+      for (int r = 0; r < KM; ++r) x[r] = snbr[(v * K + ssub[(s * KM + r) * kRC + lane]) * kRC + lane] - qv;
+      if constexpr (M == 8) {
+        float2 acc = make_float2(0.f, 0.f);
+        float acc2 = 0.f;
+#pragma unroll
+        for (int r = 0; r < KM; ++r) {
+          acc = __ffma2_rn(make_float2(row(LB + (s * 3) * KM + r), row(LB + (s * 3 + 1) * KM + r)),
+                           make_float2(x[r], x[r]), acc);
+          acc2 = fmaf(row(LB + (s * 3 + 2) * KM + r), x[r], acc2);
+        }
+        b[s][0] = acc.x;
+        b[s][1] = acc.y;
+        b[s][2] = acc2;
+      } else {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          float acc = 0.f;
+#pragma unroll
+          for (int r = 0; r < KM; ++r) acc += row(LB + (s * 3 + d) * KM + r) * x[r];
+          b[s][d] = acc;
+        }
+      }
+    }
+    float mi[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) mi[q] = S::lean ? gl[q] : sgeo[q * kRC + lane];
+    const float hi = S::lean ? gl[6] : sgeo[6 * kRC + lane];
+    const float glin = P.f_glin, g0 = 1.f - float(M) * glin, eps = P.f_eps;
+    recon_finish<float, M>(a, b, qv, mi, hi, glin, g0, eps, res);
   }
   write_block_records<float>(tile, res, live, lane, v, nv, coef, c0);
 }
 
 template <int K, int M, int KM>
-__global__ void __launch_bounds__(kRThreads) k_recon_rs(DevMesh m, DevParams P, const float* __restrict__ Qf,
+__global__ void __launch_bounds__(kRThreads, ReconSmemF<K, M, KM>::blocks) k_recon_rs(DevMesh m, DevParams P,
+                                                                                 const float* __restrict__ Qf,
                                                         float* __restrict__ coef, Control* __restrict__ ctl) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   if (m.nmesh == 1 && ctl->dt == 0.0) return;  // uniform over the grid (a batch computes every member)
