@@ -19,10 +19,12 @@
 // quadrature, closed forms (Euler and Navier-Stokes limits, S2O4 on a linear
 // ODE), exact reconstruction of linear/quadratic data, free-stream
 // preservation, conservation and the convergence order on the exact
-// density-wave solution.  Parity unpinned (readings checked only for
-// consistency): the time-step formula, the numerical collision time
-// coefficient, the far-field/wall ghost-cell maps used inside stencils and the
-// WENO epsilon.
+// density-wave solution, on tetrahedra, hexahedra and prisms (prism volumes,
+// centroids and moments against their three tetrahedra; the hybrid shell's
+// volume against the divergence theorem).  Parity unpinned (readings checked
+// only for consistency): the time-step formula, the numerical collision time
+// coefficient, the far-field/wall ghost-cell maps used inside stencils, the
+// WENO epsilon and the prism's repeated corner sub-stencil.
 #include <algorithm>
 #include <array>
 #include <cmath>
