@@ -75,6 +75,7 @@ def _load():
             lib.o_gauss_moments.argtypes = [C.c_double, C.c_double, C.c_int, d]
             lib.o_micro_slope.argtypes = [C.c_double, d, d, d]
             lib.o_boundary_state.argtypes = [d, C.c_int, d, d, d]
+            lib.o_boundary_flux.argtypes = [d, C.c_int, d, d, d, C.c_double, d, d, d, d]
             lib.o_s2o4_linear.argtypes = [C.c_int, d, C.c_double, C.c_double]
             _lib = lib
     return _lib
@@ -224,6 +225,17 @@ def boundary_state(kind: int, n, q, **params):
     n, q = _f64(n), _f64(q)
     _load().o_boundary_state(_dp(p), int(kind), _dp(n), _dp(q), _dp(o))
     return o
+
+
+def boundary_flux(kind: int, n, ql, gl, dt, **params):
+    """Flux F^n, dF/dt at a boundary Gauss point (kind 2 far field, 3 wall)
+    as the stage operator forms it, with the far side (qr, gr) it used."""
+    lib = _load()
+    p = param_array(**params)
+    F, dF, qr, gr = np.empty(5), np.empty(5), np.empty(5), np.empty((5, 3))
+    n, ql, gl = (_f64(a) for a in (n, ql, gl))
+    lib.o_boundary_flux(_dp(p), int(kind), _dp(n), _dp(ql), _dp(gl), float(dt), _dp(F), _dp(dF), _dp(qr), _dp(gr))
+    return F, dF, qr, gr
 
 
 def s2o4_linear(q, lam: float, dt: float):

@@ -19,10 +19,15 @@
 // quadrature, closed forms (Euler and Navier-Stokes limits, S2O4 on a linear
 // ODE), exact reconstruction of linear/quadratic data, free-stream
 // preservation, conservation and the convergence order on the exact
-// density-wave solution, on tetrahedra, hexahedra and prisms (prism volumes,
-// centroids and moments against their three tetrahedra; the hybrid shell's
-// volume against the divergence theorem).  Parity unpinned (readings checked
-// only for consistency): the time-step formula, the numerical collision time
+// density-wave solution, on tetrahedra, full hexahedra and prisms (prism
+// volumes, centroids and moments against their three tetrahedra; the hybrid
+// shell's volume against the divergence theorem).  The smoothness indicators
+// and nonlinear weights are pinned on tetrahedra and hexahedra by Gauss
+// quadrature of the squared derivatives and independent least-squares fits
+// over the paper's sub-stencils; the wall's far side at a Gauss point by the
+// hand-built mirror image and the symmetry it implies (no mass or energy
+// through the wall).  Parity unpinned (readings checked only for
+// consistency): the time-step formula, the numerical collision time
 // coefficient, the far-field/wall ghost-cell maps used inside stencils, the
 // WENO epsilon and the prism's repeated corner sub-stencil.
 #include <algorithm>
@@ -1147,6 +1152,28 @@ static void recon_eval(const Solver& S, int c, const V3& x, double* val, double 
   }
 }
 
+// The far side of a boundary Gauss point with outward unit normal n, from
+// the interior point value ql and gradient gl (Section 5.2).  READING: the
+// no-slip adiabatic wall mirrors the interior across the face, so the state
+// has all momentum negated and the gradient is reflected (its normal
+// component changes sign) with the momentum rows negated too; the far field
+// takes the Riemann-invariant state with zero gradient.
+static void boundary_side(const Params& P, int bc, const V3& n, const double* ql, const double gl[5][3],
+                          double* qr, double gr[5][3]) {
+  if (bc == BC_WALL) {
+    wall_state(ql, qr);
+    for (int v = 0; v < 5; ++v) {
+      double sgn = (v >= 1 && v <= 3) ? -1.0 : 1.0;
+      V3 gv = {gl[v][0], gl[v][1], gl[v][2]};
+      double dn = dot(gv, n);
+      for (int ax = 0; ax < 3; ++ax) gr[v][ax] = sgn * (gv[ax] - 2.0 * dn * n[ax]);
+    }
+  } else {
+    farfield_state(P, n, ql, qr);
+    for (int v = 0; v < 5; ++v) for (int ax = 0; ax < 3; ++ax) gr[v][ax] = 0.0;
+  }
+}
+
 // --------------------------------------------------------------------------
 // One stage: reconstruct, fluxes (Eq. flux-G with Gaussian quadrature),
 // operator L and dL/dt (Eq. finite).
@@ -1163,21 +1190,8 @@ static void stage_operator(Solver& S, double dt, std::vector<double>& L, std::ve
       double ql[5], gl[5][3], qr[5], gr[5][3];
       recon_eval(S, fa.owner, fa.xg[g], ql, gl);
       const V3& n = fa.ng_[g];
-      if (fa.nbr >= 0) {
-        recon_eval(S, fa.nbr, sub(fa.xg[g], fa.shift), qr, gr);
-      } else if (fa.bc == BC_WALL) {
-        // mirror: momentum negated, normal derivative reflected
-        wall_state(ql, qr);
-        for (int v = 0; v < 5; ++v) {
-          double sgn = (v >= 1 && v <= 3) ? -1.0 : 1.0;
-          V3 gv = {gl[v][0], gl[v][1], gl[v][2]};
-          double dn = dot(gv, n);
-          for (int ax = 0; ax < 3; ++ax) gr[v][ax] = sgn * (gv[ax] - 2.0 * dn * n[ax]);
-        }
-      } else {
-        farfield_state(S.P, n, ql, qr);
-        for (int v = 0; v < 5; ++v) for (int ax = 0; ax < 3; ++ax) gr[v][ax] = 0.0;
-      }
+      if (fa.nbr >= 0) recon_eval(S, fa.nbr, sub(fa.xg[g], fa.shift), qr, gr);
+      else boundary_side(S.P, fa.bc, n, ql, gl, qr, gr);
       FluxOut fo = gks_flux_global(S.P, n, ql, gl, qr, gr, dt);
       for (int v = 0; v < 5; ++v) { Fs[v] += fa.wa[g] * fo.F[v]; Ds[v] += fa.wa[g] * fo.dF[v]; }
     }
@@ -1402,6 +1416,24 @@ void o_flux_point(const double* params, const double* n, const double* ql, const
   V3 nn = {n[0], n[1], n[2]};
   FluxOut o = gks_flux_global(P, nn, ql, GL, qr, GR, dt);
   for (int i = 0; i < 5; ++i) { F[i] = o.F[i]; dF[i] = o.dF[i]; }
+}
+
+// Flux at a boundary Gauss point exactly as the stage operator forms it:
+// the far side from boundary_side (bc 2 far field, 3 wall), then the
+// gas-kinetic flux.  gl: [5][3] interior gradient; qr_out, gr_out (may be
+// NULL) receive the far side.
+void o_boundary_flux(const double* params, int bc, const double* n, const double* ql, const double* gl, double dt,
+                     double* F, double* dF, double* qr_out, double* gr_out) {
+  Params P;
+  set_params(P, params);
+  double GL[5][3], GR[5][3], qr[5];
+  for (int v = 0; v < 5; ++v) for (int a = 0; a < 3; ++a) GL[v][a] = gl[v * 3 + a];
+  V3 nn = {n[0], n[1], n[2]};
+  boundary_side(P, bc, nn, ql, GL, qr, GR);
+  FluxOut o = gks_flux_global(P, nn, ql, GL, qr, GR, dt);
+  for (int i = 0; i < 5; ++i) { F[i] = o.F[i]; dF[i] = o.dF[i]; }
+  if (qr_out) for (int i = 0; i < 5; ++i) qr_out[i] = qr[i];
+  if (gr_out) for (int v = 0; v < 5; ++v) for (int a = 0; a < 3; ++a) gr_out[v * 3 + a] = GR[v][a];
 }
 
 // Normalized 1D moments <u^k>, k < 12: half 0 full, +1 u>0, -1 u<0.
