@@ -110,6 +110,34 @@ def prism_cube(n: int, length: float = 2.0, jitter: float = 0.0, seed: int = 0):
     return xyz, cells, periods
 
 
+def hex_cube(n: int, length: float = 2.0, jitter: float = 0.0, seed: int = 0):
+    """Return (xyz, cells[n^3, 8], periods[3]): the periodic cube [0,L]^3 as
+    an n^3 lattice of hexahedra (nodes 0-3 the lower quad counter-clockwise
+    seen from above, 4-7 the upper quad in the same order, so the trilinear
+    map has a positive Jacobian).  Same node jitter as ``kuhn_cube``; jittered
+    hexahedra have non-planar faces."""
+    h = length / n
+    m = n + 1
+    ii, jj, kk = np.meshgrid(np.arange(m), np.arange(m), np.arange(m), indexing="ij")
+    xyz = np.stack([ii, jj, kk], axis=-1).reshape(-1, 3).astype(np.float64) * h
+    if jitter > 0.0:
+        rng = np.random.default_rng(seed)
+        off = rng.uniform(-jitter * h, jitter * h, size=xyz.shape)
+        interior = np.all((xyz > 0.5 * h) & (xyz < length - 0.5 * h), axis=1)
+        xyz[interior] += off[interior]
+
+    def nid(i, j, k):
+        return (i * m + j) * m + k
+
+    ci, cj, ck = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    ci, cj, ck = ci.ravel(), cj.ravel(), ck.ravel()
+    cells = np.stack([nid(ci, cj, ck), nid(ci + 1, cj, ck), nid(ci + 1, cj + 1, ck), nid(ci, cj + 1, ck),
+                      nid(ci, cj, ck + 1), nid(ci + 1, cj, ck + 1), nid(ci + 1, cj + 1, ck + 1),
+                      nid(ci, cj + 1, ck + 1)], axis=1).astype(np.int64)
+    periods = np.array([length, length, length], dtype=np.float64)
+    return xyz, cells, periods
+
+
 def prism_tets(cells: np.ndarray) -> np.ndarray:
     """The three tetrahedra [n, 3, 4] that make up each prism (nodes
     2 = 3, 6 = 7) with planar side faces: (0 1 2 4), (1 2 4 5), (2 4 5 6)."""
