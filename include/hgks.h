@@ -265,18 +265,26 @@ int hgks_profile(hgks_solver* s, int n_steps, double t_end, double dt_fixed, dou
 #define HGKS_NOALLOC_MAX_CELLS 4194304
 
 /* The CFL time step of a state the caller holds on the device, computed
- * without allocating anything: for callers that cannot call cudaMalloc at
- * that point, such as code running while a stream is captured into a graph,
- * hosts whose device memory belongs to another allocator, or loops that must
- * not pay an allocation's implicit synchronisation.  The paper has no
- * counterpart; it is the time-step reduction of hgks_step with its scratch
- * moved into a fixed device array inside the library.
+ * without allocating anything.  For callers that cannot allocate device
+ * memory when they need the step: hosts whose device memory belongs to
+ * another allocator that forbids foreign cudaMalloc/cudaFree calls, and loops
+ * that cannot accept the device-wide synchronisation of cudaFree.  The paper
+ * has no counterpart; it is the time-step reduction of hgks_step with its
+ * scratch moved into a fixed device array inside the library.
  *   q       device pointer, [n_cells][5] conservative cell averages
  *   hdt     device pointer, [n_cells] length scales 3|cell|/|surface|
- *   params  host pointer; gamma, cfl, mu_ref, T_ref, visc_exp are used
+ *           (hgks_mesh_geometry gives them in caller order)
+ *   params  host pointer, checked as hgks_init checks it (HGKS_EINVAL);
+ *           gamma, cfl, mu_ref, T_ref, visc_exp are used
  *   dt_out  device pointer to one double: cfl min_i of the bound documented
- *           for hgks_params.cfl (written by the GPU, stream-ordered)
+ *           for hgks_params.cfl, written by the GPU, stream-ordered.  NaN if
+ *           some cell has no bound: a non-finite value, or a non-positive
+ *           density or pressure.
  *   stream  cudaStream_t to launch on (NULL: the legacy default stream)
+ * The bound is always evaluated in binary64.  It equals the step hgks_step
+ * takes for an HGKS_FP64 solver; an HGKS_FP32_MIXED solver evaluates its
+ * bound in binary32 from its binary32 state copy, so its step can differ by
+ * about 1e-7 relative.
  * Scratch: a file-scope 16384-double (128 KiB) device array, one per GPU that
  * loads the library, held until the process exits; n_cells above
  * HGKS_NOALLOC_MAX_CELLS is rejected with HGKS_EINVAL.  The first call on a

@@ -97,19 +97,6 @@ cudaError_t up(T* dst, const std::vector<T>& src, cudaStream_t st) {
   return cudaMemcpyAsync(dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, st);
 }
 
-int check_params(const hgks_params* p) {
-  if (!p) return fail(HGKS_EINVAL, "params is NULL");
-  if (!(p->gamma > 1.0 && p->gamma < 5.0 / 3.0 + 1e-12)) return fail(HGKS_EINVAL, "gamma must lie in (1, 5/3]");
-  if (!(p->cfl > 0.0)) return fail(HGKS_EINVAL, "cfl must be positive");
-  if (!(p->mu_ref >= 0.0) || !(p->tau_num_c >= 0.0)) return fail(HGKS_EINVAL, "mu_ref and tau_num_c must be >= 0");
-  if (p->mu_ref > 0.0 && p->visc_exp != 0.0 && !(p->T_ref > 0.0)) return fail(HGKS_EINVAL, "T_ref must be positive");
-  if (!(p->Pr > 0.0)) return fail(HGKS_EINVAL, "Pr must be positive");
-  if (!(p->weno_eps > 0.0)) return fail(HGKS_EINVAL, "weno_eps must be positive");
-  if (!(p->weno_gamma_lin > 0.0 && p->weno_gamma_lin < 0.125)) return fail(HGKS_EINVAL, "weno_gamma_lin must lie in (0, 1/8)");
-  if (p->precision != HGKS_FP64 && p->precision != HGKS_FP32_MIXED) return fail(HGKS_EINVAL, "unknown precision");
-  if (p->persistent != 0 && p->persistent != 1) return fail(HGKS_EINVAL, "persistent must be 0 or 1");
-  return HGKS_OK;
-}
 
 // internal SoA [5][stride] at the member's offset -> member's caller order [n][5]
 void to_caller(const Member& mb, const double* h, int64_t stride, double* q) {
@@ -123,6 +110,21 @@ void to_caller(const Member& mb, const double* h, int64_t stride, double* q) {
 
 namespace hgks {
 void set_last_error(const std::string& msg) { g_err = msg; }
+
+// Parameter checks shared by every entry point that takes hgks_params.
+int check_params(const hgks_params* p) {
+  if (!p) return fail(HGKS_EINVAL, "params is NULL");
+  if (!(p->gamma > 1.0 && p->gamma < 5.0 / 3.0 + 1e-12)) return fail(HGKS_EINVAL, "gamma must lie in (1, 5/3]");
+  if (!(p->cfl > 0.0)) return fail(HGKS_EINVAL, "cfl must be positive");
+  if (!(p->mu_ref >= 0.0) || !(p->tau_num_c >= 0.0)) return fail(HGKS_EINVAL, "mu_ref and tau_num_c must be >= 0");
+  if (p->mu_ref > 0.0 && p->visc_exp != 0.0 && !(p->T_ref > 0.0)) return fail(HGKS_EINVAL, "T_ref must be positive");
+  if (!(p->Pr > 0.0)) return fail(HGKS_EINVAL, "Pr must be positive");
+  if (!(p->weno_eps > 0.0)) return fail(HGKS_EINVAL, "weno_eps must be positive");
+  if (!(p->weno_gamma_lin > 0.0 && p->weno_gamma_lin < 0.125)) return fail(HGKS_EINVAL, "weno_gamma_lin must lie in (0, 1/8)");
+  if (p->precision != HGKS_FP64 && p->precision != HGKS_FP32_MIXED) return fail(HGKS_EINVAL, "unknown precision");
+  if (p->persistent != 0 && p->persistent != 1) return fail(HGKS_EINVAL, "persistent must be 0 or 1");
+  return HGKS_OK;
+}
 }  // namespace hgks
 
 extern "C" {
@@ -509,7 +511,7 @@ int make_solver(hgks_dmesh* d, const hgks_params* params, const double* const* q
 int create_solver(hgks_mesh* const* meshes, int n, const hgks_params* params, const double* const* q0,
                   hgks_solver** out) {
   *out = nullptr;
-  int rc = check_params(params);
+  int rc = hgks::check_params(params);
   if (rc) return rc;
   cudaStream_t st = nullptr;
   bool own = false;
@@ -803,7 +805,7 @@ int64_t hgks_dmesh_info(const hgks_dmesh* d, int what) {
 int hgks_init_shared(hgks_dmesh* dmesh, const hgks_params* params, const double* q0, hgks_solver** out) {
   if (!dmesh || !out || !q0) return fail(HGKS_EINVAL, "NULL argument");
   *out = nullptr;
-  int rc = check_params(params);
+  int rc = hgks::check_params(params);
   if (rc) return rc;
   cudaStream_t st = nullptr;
   bool own = false;

@@ -7,6 +7,8 @@
 
 #include <cuda_runtime.h>
 
+#include "hgks.h"
+
 namespace hgks {
 
 // Read-only mesh arrays in device memory (layouts as in mesh_builder.h).
@@ -116,6 +118,8 @@ struct DevWork {
 
 // Message returned by hgks_last_error() on this thread.
 void set_last_error(const std::string& msg);
+// HGKS_OK, or HGKS_EINVAL with the message set, for out-of-range parameters.
+int check_params(const hgks_params* p);
 
 // Set the step size of every member (tuning and test paths).
 void launch_setdt(const DevMesh& m, const DevWork& w, double dt, cudaStream_t s);

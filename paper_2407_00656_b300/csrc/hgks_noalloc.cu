@@ -2,13 +2,13 @@
 // no allocation at all.
 //
 // Some callers cannot allocate device memory at the moment they need the time
-// step: code that runs while a CUDA stream is being captured into a graph
-// (cudaMalloc is not a stream operation and breaks or serialises the capture),
-// hosts whose device memory is owned by another allocator that forbids foreign
-// cudaMalloc/cudaFree calls, and real-time loops where an allocation's implicit
-// device synchronisation is not acceptable.  hgks_cfl_dt_noalloc serves them:
-// it is a variant of the solver's time-step reduction whose per-block partial
-// minima live in a fixed, file-scope device array instead of solver memory.
+// step: hosts whose device memory is owned by another allocator that forbids
+// foreign cudaMalloc/cudaFree calls (a pool sized up front, a framework that
+// accounts for every byte), and loops that cannot accept cudaFree's implicit
+// device-wide synchronisation.  hgks_cfl_dt_noalloc serves them: it is a
+// variant of the solver's time-step reduction whose per-block partial minima
+// live in a fixed, file-scope device array instead of solver memory.  The
+// bound is always evaluated in binary64.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -42,28 +42,34 @@ struct DtParams {
 };
 
 // Local bound h/(|U| + c), and with viscosity also rho h^2/(2 mu); T = p/rho.
+// NaN for a state that has no bound: a non-finite value, or a non-positive
+// density or pressure.
 __device__ __forceinline__ double local_bound(const double* q, double h, const DtParams& P) {
   const double ri = 1.0 / q[0];
   const double u = q[1] * ri, v = q[2] * ri, w = q[3] * ri;
   const double u2 = u * u + v * v + w * w;
   const double p = (P.gamma - 1.0) * (q[4] - 0.5 * q[0] * u2);
+  if (!(q[0] > 0.0) || !(p > 0.0) || !isfinite(u2) || !isfinite(p)) return NAN;
   double b = h / (sqrt(u2) + sqrt(P.gamma * p * ri));
   if (P.mu_ref > 0.0) {
     const double mu = P.visc_exp != 0.0 ? P.mu_ref * pow(p * ri / P.T_ref, P.visc_exp) : P.mu_ref;
     b = fmin(b, q[0] * h * h / (2.0 * mu));
   }
-  return (b >= 0.0) ? b : INFINITY;
+  return b;
 }
+
+// Minimum that keeps a NaN (fmin would drop it).
+__device__ __forceinline__ double min_nan(double a, double b) { return (a != a || b != b) ? NAN : fmin(a, b); }
 
 __device__ __forceinline__ double block_min(double v) {
   __shared__ double red[kThreads / 32];
-  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  for (int o = 16; o > 0; o >>= 1) v = min_nan(v, __shfl_xor_sync(0xffffffffu, v, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
   double x = INFINITY;
   if (threadIdx.x < 32) {
     x = threadIdx.x < kThreads / 32 ? red[threadIdx.x] : INFINITY;
-    for (int o = 16; o > 0; o >>= 1) x = fmin(x, __shfl_xor_sync(0xffffffffu, x, o));
+    for (int o = 16; o > 0; o >>= 1) x = min_nan(x, __shfl_xor_sync(0xffffffffu, x, o));
   }
   return x;  // valid in thread 0
 }
@@ -78,11 +84,12 @@ __global__ void __launch_bounds__(kThreads) k_dt_partials(const double* __restri
   if (threadIdx.x == 0) partial[blockIdx.x] = b;
 }
 
-// Phase 2: one block reduces the nb partials and writes cfl * min.
+// Phase 2: one block reduces the nb partials and writes cfl * min (NaN if
+// any cell had no bound).
 __global__ void __launch_bounds__(kThreads) k_dt_final(const double* __restrict__ partial, int nb, double cfl,
                                                        double* __restrict__ dt_out) {
   double b = INFINITY;
-  for (int k = threadIdx.x; k < nb; k += kThreads) b = fmin(b, partial[k]);
+  for (int k = threadIdx.x; k < nb; k += kThreads) b = min_nan(b, partial[k]);
   b = block_min(b);
   if (threadIdx.x == 0) *dt_out = cfl * b;
 }
@@ -103,7 +110,8 @@ int hgks_cfl_dt_noalloc(const double* q, const double* hdt, int64_t n_cells, con
   if (n_cells > HGKS_NOALLOC_MAX_CELLS)
     return fail(HGKS_EINVAL, "n_cells " + std::to_string(n_cells) + " exceeds the fixed scratch limit of " +
                                  std::to_string((long long)HGKS_NOALLOC_MAX_CELLS) + " cells");
-  if (!(params->gamma > 1.0) || !(params->cfl > 0.0)) return fail(HGKS_EINVAL, "gamma must exceed 1 and cfl be positive");
+  const int prc = hgks::check_params(params);  // the same checks as hgks_init
+  if (prc) return prc;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(HGKS_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));

@@ -214,3 +214,23 @@ def test_full_size_jittered_mesh_one_step():
     s.step(1)
     o.step(1)
     assert relerr(s.read()[0], o.get_state()[0]) < TOL
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(mu_ref=2e-3, Pr=0.72, tau_c=1.0)], ids=["inviscid", "viscous"])
+def test_periodic_jittered_hexahedra_stage_operator_and_steps(kw):
+    """Full hexahedra with non-planar faces on a periodic cube (7^3 = 343
+    cells, a ragged last block): stage operator and three full steps."""
+    xyz, cells, per = I.hex_cube(7, jitter=0.15, seed=9)
+    q = I.random_smooth_state(xyz, cells, seed=5, amp=0.08)
+    s, o = both(xyz, cells, per, q=q, **kw)
+    L, dL = s.stage_operator(0.01)
+    Lo, dLo = o.operator(0.01)
+    assert relerr(L, Lo) < TOL
+    assert relerr(dL, dLo) < TOL
+    s.step(3)
+    o.step(3)
+    qg, t, n = s.read()
+    qo, to, no = o.get_state()
+    assert n == no == 3 and abs(t - to) <= 1e-15 * to
+    assert relerr(qg, qo) < TOL
+    s.close()
