@@ -261,6 +261,20 @@ int hgks_stage_operator(hgks_solver* s, double dt, double* L_out, double* dL_out
  * flux (both stages) and the two S2O4 updates.  Synchronises every step. */
 int hgks_profile(hgks_solver* s, int n_steps, double t_end, double dt_fixed, double* ms_out);
 
+/* Test hooks for the failure paths (no counterpart in the paper).
+ * hgks_test_barrier_limit: the clock cycles a grid barrier of the persistent
+ * launch (hgks_params.persistent) waits before it gives up, for the solver's
+ * later hgks_step calls; cycles < 0 restores the default 2^31 (about a
+ * second).  A barrier that gives up ends the launch, and hgks_sync /
+ * hgks_read return HGKS_ETIMEOUT until hgks_write resets the state.
+ * Synchronises.  Errors: HGKS_EINVAL (NULL solver).
+ * hgks_test_fail_alloc: the library's n-th device allocation from now on
+ * (n = 0: the next one) fails as an exhausted memory pool would, so the
+ * creating call returns HGKS_ENOMEM and releases what it had taken; n < 0
+ * switches the hook off.  Process-wide; returns HGKS_OK. */
+int hgks_test_barrier_limit(hgks_solver* s, int64_t cycles);
+int hgks_test_fail_alloc(int n);
+
 /* Largest n_cells accepted by hgks_cfl_dt_noalloc. */
 #define HGKS_NOALLOC_MAX_CELLS 4194304
 

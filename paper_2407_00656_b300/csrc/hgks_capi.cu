@@ -243,9 +243,18 @@ void prepare_pool() {
   done[dev] = true;
 }
 
+// Test hook (hgks_test_fail_alloc): the number of device allocations still to
+// succeed before one is made to fail, or -1.
+std::atomic<int> g_fail_alloc{-1};
+
 int alloc_on(void** p, size_t bytes, cudaStream_t st, const char* what) {
   prepare_pool();
-  cudaError_t e = cudaMallocAsync(p, bytes, st);
+  int k = g_fail_alloc.load();
+  while (k >= 0 && !g_fail_alloc.compare_exchange_weak(k, k - 1)) {
+  }
+  // k == 0: this allocation is the one the test asked to fail, as an
+  // exhausted pool would (nothing is allocated)
+  cudaError_t e = k == 0 ? cudaErrorMemoryAllocation : cudaMallocAsync(p, bytes, st);
   if (e != cudaSuccess) {
     *p = nullptr;
     cudaGetLastError();
@@ -459,6 +468,7 @@ int make_solver(hgks_dmesh* d, const hgks_params* params, const double* const* q
     dp.flux_variant = dm.nf < per_sm * sms * 128 ? 1 : 0;
   }
   dp.recon_variant = 0;
+  dp.bar_cycles = hgks::kBarrierCycles;
   hgks::prepare_kernels(dm, s->precision);
   // initial states: each member's caller-order states are copied into Q*
   // (free until the first step) and permuted into Q on the device; the ghost
@@ -564,6 +574,9 @@ int create_solver(hgks_mesh* const* meshes, int n, const hgks_params* params, co
   return HGKS_OK;
 }
 
+const char* const kStageMsg = "a reconstruction block's bounded wait for its staged copies ran out";
+const char* const kBarMsg = "a grid barrier of the persistent launch ran out of its bounded wait";
+
 int read_flags(hgks_solver* s, int only, hgks::Control* first) {
   std::vector<hgks::Control> c(s->members().size());
   HGKS_CUDA(cudaMemcpy(c.data(), s->dw.ctl, sizeof(hgks::Control) * c.size(), cudaMemcpyDeviceToHost),
@@ -571,11 +584,13 @@ int read_flags(hgks_solver* s, int only, hgks::Control* first) {
   if (first) *first = c[only >= 0 ? only : 0];
   for (size_t i = 0; i < c.size(); ++i) {
     if (only >= 0 && (int)i != only) continue;
-    if (c[i].flags & hgks::FLAG_TIMEOUT) return fail(HGKS_ETIMEOUT, "a bounded wait for staged copies ran out");
+    if (c[i].flags & hgks::FLAG_BAR_TIMEOUT) return fail(HGKS_ETIMEOUT, kBarMsg);
+    if (c[i].flags & hgks::FLAG_TIMEOUT) return fail(HGKS_ETIMEOUT, kStageMsg);
     if (c[i].flags & hgks::FLAG_NONFINITE) return fail(HGKS_ENONFINITE, "a step produced a non-finite cell average");
   }
-  // a staging timeout is recorded on member 0 for the whole solver
-  if (only > 0 && (c[0].flags & hgks::FLAG_TIMEOUT)) return fail(HGKS_ETIMEOUT, "a bounded wait for staged copies ran out");
+  // timeouts are recorded on member 0 for the whole solver
+  if (only > 0 && (c[0].flags & hgks::FLAG_BAR_TIMEOUT)) return fail(HGKS_ETIMEOUT, kBarMsg);
+  if (only > 0 && (c[0].flags & hgks::FLAG_TIMEOUT)) return fail(HGKS_ETIMEOUT, kStageMsg);
   return HGKS_OK;
 }
 
@@ -740,6 +755,18 @@ int hgks_set_tuning(hgks_solver* s, int flux_variant, int recon_variant) {
     cudaGraphExecDestroy(s->graph);
     s->graph = nullptr;
   }
+  return HGKS_OK;
+}
+
+int hgks_test_barrier_limit(hgks_solver* s, int64_t cycles) {
+  if (!s) return fail(HGKS_EINVAL, "NULL solver");
+  HGKS_CUDA(cudaStreamSynchronize(s->stream), "waiting for queued work");
+  s->dp.bar_cycles = cycles < 0 ? hgks::kBarrierCycles : (long long)cycles;
+  return HGKS_OK;
+}
+
+int hgks_test_fail_alloc(int n) {
+  g_fail_alloc.store(n < 0 ? -1 : n);
   return HGKS_OK;
 }
 

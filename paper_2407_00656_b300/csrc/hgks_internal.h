@@ -53,7 +53,11 @@ struct DevParams {
   // kernel variants chosen by the autotuner:
   int flux_variant;   // 0: one thread per face, 1: one thread per Gauss point
   int recon_variant;  // 0: rows staged by bulk async copies, 1: rows read directly
+  long long bar_cycles;  // clock cycles a grid barrier of the persistent launch waits before giving up
 };
+
+// Default wait of a grid barrier: 2^31 cycles, about a second at 2 GHz.
+constexpr long long kBarrierCycles = 1LL << 31;
 
 // Fill kq, kqi and the binary32 copies of the parameters.
 inline void fill_float_params(DevParams& p) {
@@ -94,7 +98,9 @@ struct Control {
   int pad;
 };
 
-enum { FLAG_NONFINITE = 1, FLAG_TIMEOUT = 2 };
+// FLAG_TIMEOUT: a reconstruction block's wait for its bulk copies ran out;
+// FLAG_BAR_TIMEOUT: a grid barrier of the persistent launch ran out.
+enum { FLAG_NONFINITE = 1, FLAG_TIMEOUT = 2, FLAG_BAR_TIMEOUT = 4 };
 
 // Grid-wide barrier state of a persistent launch (zeroed before each launch).
 struct GridBar {

@@ -1023,8 +1023,13 @@ __device__ __forceinline__ void recon_block(const DevMesh& m, const DevParams& P
   if constexpr (STAGE) {
     const bool ok = __syncthreads_and(mbar_wait_bounded(&bar, 0));
     if (!ok) {
+      // The block's copies (its own inverse rows, under 100 KB) have not landed
+      // within about a second, which only a stalled memory system explains.
+      // Flag it, give the copies one more bounded wait, and leave: the block
+      // may then exit with copies outstanding, which it accepts rather than
+      // hang the device; the host reports HGKS_ETIMEOUT.
       if (threadIdx.x == 0) atomicOr(&ctl->flags, FLAG_TIMEOUT);
-      mbar_wait_bounded(&bar, 0);  // copies in flight: a second bounded wait before leaving
+      mbar_wait_bounded(&bar, 0);
       return;
     }
     if constexpr (sizeof(Real) == 4) {
@@ -1739,10 +1744,12 @@ __device__ __forceinline__ unsigned ld_volatile(const unsigned* p) {
 }
 
 // Grid-wide barrier of a cooperative launch (all blocks are resident), with a
-// bounded wait: false after about 2^31 clock cycles (~1 s), with FLAG_TIMEOUT
-// set on member 0; the caller then leaves the kernel, and so does every
-// other block at its own bounded wait.
-__device__ bool grid_sync(GridBar* b, Control* ctl) {
+// bounded wait: false after `limit` clock cycles (2^31 by default, about a
+// second), with FLAG_BAR_TIMEOUT set on member 0; the caller then leaves the
+// kernel, and so does every other block at its own bounded wait (the last
+// block to arrive never waits, so each barrier lets at most one block through
+// once another has left).
+__device__ bool grid_sync(GridBar* b, Control* ctl, long long limit) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1756,8 +1763,8 @@ __device__ bool grid_sync(GridBar* b, Control* ctl) {
     } else {
       const long long t0 = clock64();
       while (ld_volatile(&b->gen) == g) {
-        if (clock64() - t0 > (1LL << 31)) {
-          atomicOr(&ctl->flags, FLAG_TIMEOUT);
+        if (clock64() - t0 > limit) {
+          atomicOr(&ctl->flags, FLAG_BAR_TIMEOUT);
           ok = 0;
           break;
         }
@@ -1786,14 +1793,14 @@ __global__ void __launch_bounds__(kRThreads, sizeof(Real) == 4 ? 2 : 1)
   for (int step = 0; step < nsteps; ++step) {
     if (blockIdx.x == 0)
       for (int i = threadIdx.x; i < m.nmesh; i += blockDim.x) finalize_one<true>(ctl + i, P.cfl);
-    if (!grid_sync(w.bar, ctl)) return;
+    if (!grid_sync(w.bar, ctl, P.bar_cycles)) return;
     const bool idle = m.nmesh == 1 && ldm<true>(&ctl->dt) == 0.0;  // the same in every block
     for (int stage = 0; stage < 2; ++stage) {
       double* Qin = stage == 0 ? w.Q : w.Qs;
       if (m.ng) {
         if (!idle)
           for (int64_t g = gt; g < m.ng; g += nthr) ghost_one<true>(m, P, Qin, Qf, ctl, g);
-        if (!grid_sync(w.bar, ctl)) return;
+        if (!grid_sync(w.bar, ctl, P.bar_cycles)) return;
       }
       if (!idle) {
         for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -1802,10 +1809,10 @@ __global__ void __launch_bounds__(kRThreads, sizeof(Real) == 4 ? 2 : 1)
           __syncthreads();  // the next tile reuses the shared memory
         }
       }
-      if (!grid_sync(w.bar, ctl)) return;
+      if (!grid_sync(w.bar, ctl, P.bar_cycles)) return;
       if (!idle)
         for (int64_t f = gt; f < m.nf; f += nthr) flux_face<Real, G, VISC, true>(m, P, coef, Fs, ctl, f);
-      if (!grid_sync(w.bar, ctl)) return;
+      if (!grid_sync(w.bar, ctl, P.bar_cycles)) return;
       if (stage == 0) {
         if (!idle)
           for (int64_t c = gt; c < m.nc; c += nthr) {
@@ -1825,7 +1832,7 @@ __global__ void __launch_bounds__(kRThreads, sizeof(Real) == 4 ? 2 : 1)
           __syncthreads();  // the reduction's shared buffer is reused
         }
       }
-      if (!grid_sync(w.bar, ctl)) return;
+      if (!grid_sync(w.bar, ctl, P.bar_cycles)) return;
     }
   }
 }

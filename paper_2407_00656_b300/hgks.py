@@ -63,7 +63,8 @@ EXPORTS = ("hgks_params_default", "hgks_mesh_create", "hgks_mesh_destroy", "hgks
            "hgks_batch_init", "hgks_members", "hgks_write", "hgks_member_write", "hgks_step", "hgks_query",
            "hgks_sync", "hgks_read", "hgks_member_read", "hgks_stage_operator", "hgks_profile", "hgks_solver_bytes",
            "hgks_tuning", "hgks_set_tuning", "hgks_destroy", "hgks_last_error", "hgks_cfl_dt_noalloc",
-           "hgks_dmesh_create", "hgks_dmesh_release", "hgks_dmesh_info", "hgks_init_shared")
+           "hgks_dmesh_create", "hgks_dmesh_release", "hgks_dmesh_info", "hgks_init_shared",
+           "hgks_test_barrier_limit", "hgks_test_fail_alloc")
 
 
 def lib():
@@ -104,6 +105,10 @@ def lib():
             L.hgks_read.argtypes = [vp, dp, dp, C.POINTER(C.c_int64)]
             L.hgks_stage_operator.argtypes = [vp, C.c_double, dp, dp]
             L.hgks_profile.argtypes = [vp, C.c_int, C.c_double, C.c_double, dp]
+            L.hgks_test_barrier_limit.argtypes = [vp, C.c_int64]
+            L.hgks_test_barrier_limit.restype = C.c_int
+            L.hgks_test_fail_alloc.argtypes = [C.c_int]
+            L.hgks_test_fail_alloc.restype = C.c_int
             L.hgks_cfl_dt_noalloc.argtypes = [vp, vp, C.c_int64, C.POINTER(hgks_params), vp, vp]
             L.hgks_cfl_dt_noalloc.restype = C.c_int
             L.hgks_dmesh_create.argtypes = [vp, vp, C.POINTER(vp)]
@@ -159,6 +164,12 @@ def cfl_dt_noalloc(q_ptr: int, hdt_ptr: int, n_cells: int, params: hgks_params, 
     q [n][5], hdt [n], result written to dt_ptr on the GPU."""
     _check(lib().hgks_cfl_dt_noalloc(C.c_void_p(q_ptr), C.c_void_p(hdt_ptr), int(n_cells), C.byref(params),
                                      C.c_void_p(dt_ptr), C.c_void_p(stream or None)), "hgks_cfl_dt_noalloc")
+
+
+def test_fail_alloc(n: int) -> None:
+    """hgks_test_fail_alloc: make the library's n-th device allocation from now
+    on fail (n = 0: the next one); n < 0 switches the hook off."""
+    _check(lib().hgks_test_fail_alloc(int(n)), "hgks_test_fail_alloc")
 
 
 class Mesh:
@@ -357,6 +368,11 @@ class Solver:
 
     def step(self, n: int = 1, t_end: float = 0.0, dt_fixed: float = 0.0):
         _check(lib().hgks_step(self._h, int(n), float(t_end), float(dt_fixed)), "hgks_step")
+
+    def test_barrier_limit(self, cycles: int):
+        """hgks_test_barrier_limit: wait limit (clock cycles) of the persistent
+        launch's grid barriers; negative restores the default."""
+        _check(lib().hgks_test_barrier_limit(self._h, int(cycles)), "hgks_test_barrier_limit")
 
     def sync(self):
         _check(lib().hgks_sync(self._h), "hgks_sync")
