@@ -38,14 +38,21 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# Executed binary64 operations per face of the FP64 flux kernel
-# k_flux<double, 3, inviscid> (sass dadd + dmul + 2 dfma per launch, divided
-# by the faces of the launch, ncu on the 32^3 x 6 mesh, 393,216 faces), and
-# its DRAM bytes per face (dram__bytes_read + dram__bytes_write of one launch
-# on the 40^3 x 6 mesh, 768,000 faces, larger than L2; the traffic grows with
-# the faces).  Set to None when the kernel changes until measured again.
-FP64_FLOPS_PER_FACE_INVISCID = 4786  # 1881.9 Mflop per launch / 393216 faces
-FP64_FLUX_DRAM_BYTES_PER_FACE = 469.0  # (312.29 + 47.90) MB / 768000 faces
+# Executed operations per unit of the dominant kernels as built, from the ncu
+# operation counts summarised under profiles/ (file named in each entry), and
+# DRAM bytes per unit where a capture measured them.  "sha" is the digest of
+# csrc/hgks_kernels.cu that the counts were taken on: when the source has
+# changed since, the line carries "counts_stale": true and no traffic.
+# Flops: binary64 2 dfma + dadd + dmul (FP64 path), binary32 2 ffma + fadd +
+# fmul (mixed path), per launch divided by the units of the launch.
+ROOF_TABLE = {
+    ("k_flux", "fp64", 3, False): dict(unit="face", flop=4786, dram=469.0, sha="r1-erfcx",
+                                       src="profiles/kernels_fp64_density40.md"),
+    ("k_flux", "fp64", 4, True): dict(unit="face", flop=14149, dram=None, sha="r1-erfcx",
+                                      src="profiles/flux_fp64_viscous_sphere24.md (per Gauss point variant)"),
+    ("k_flux", "mixed", 3, False): dict(unit="face", flop=4437, dram=341.0, sha="r1-erfcx",
+                                        src="profiles/kernels_mixed_density40.md (per Gauss point variant)"),
+}
 # Algorithmic bytes per cell of one binary32 reconstruction launch (k_recon_rs)
 # on tetrahedra: binary64 pseudo-inverse rows (9K + 3 M KM) x 8 B, sub-stencil
 # positions M KM, stencil indices 4K, second moments and 1/h 7 x 8 B, the
@@ -56,6 +63,38 @@ def recon_rs_bytes_per_cell(K: int, M: int = 4, KM: int = 6) -> int:
 
 
 FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12  # SMs x DFMA/clk x 2 flop x max SM clock
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x 2 flop x max SM clock
+
+
+def kernel_source_digest() -> str:
+    import hashlib
+
+    p = os.path.join(ROOT, "paper_2407_00656_b300", "csrc", "hgks_kernels.cu")
+    with open(p, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:12]
+
+
+def flux_roofline(precision: str, G: int, viscous: bool, faces: int, ms_per_launch: float):
+    """roofline object of the flux kernel from the operation table."""
+    peak = FP64_PEAK_TFLOPS if precision == "fp64" else FP32_PEAK_TFLOPS
+    r = {"bound": "alu", "unit": "TFLOP/s", "peak": peak,
+         "kernel": f"k_flux ({'binary64' if precision == 'fp64' else 'binary32'}, {G} Gauss points, "
+                   f"{'viscous' if viscous else 'inviscid'})",
+         "peak_source": ("derived: 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz" if precision == "fp64" else
+                         "derived: 148 SMs x 128 FP32 lanes x 2 flop x 2.032 GHz"),
+         "achieved": None, "frac": None, "traffic": None, "ms_per_launch": ms_per_launch}
+    e = ROOF_TABLE.get(("k_flux", precision, G, viscous))
+    if e is None or not ms_per_launch:
+        return r
+    ach = e["flop"] * faces / (ms_per_launch * 1e-3) / 1e12
+    r.update({"achieved": ach, "frac": ach / peak, "flop_per_launch": e["flop"] * faces,
+              "flop_per_face": e["flop"], "counts_source": e["src"]})
+    stale = e["sha"] != kernel_source_digest()
+    r["counts_stale"] = stale
+    if e["dram"] and not stale:
+        r["traffic"] = e["dram"] * faces
+        r["traffic_source"] = "ncu dram bytes per face of one launch, times the faces"
+    return r
 
 
 def _hbm_peak():
@@ -185,8 +224,12 @@ def replica_throughput(cells: int, steps: int, world: int, seconds: float) -> fl
     return cells * steps * world / seconds
 
 
-def cpu_baseline(w, budget_steps: int = 3):
-    """The CPU oracle as it stands, all host cores, on one step of the same mesh."""
+def cpu_baseline(w, H=None, budget_steps: int = 3):
+    """The CPU oracle as it stands, all host cores, on `budget_steps` steps of
+    the same mesh.  With the library H, the GPU FP64 and mixed paths take the
+    same steps from the same state and their differences from the oracle's
+    state are reported (the parity metric of the GPU tests: max |gpu - oracle|
+    over cells / max |oracle|, per variable; and the volume-weighted L1)."""
     import oracle
 
     cores = os.cpu_count() or 1
@@ -198,9 +241,25 @@ def cpu_baseline(w, budget_steps: int = 3):
     o.step(budget_steps)
     dt = time.perf_counter() - t0
     nc = len(w["cells"])
-    return {"value": nc * budget_steps / dt, "unit": "cell-updates/s", "cores": oracle.get_threads(),
-            "kind": "oracle", "sample": f"{budget_steps} S2O4 step(s) of the full {nc}-cell mesh, FP64, "
-                                        f"{oracle.get_threads()} OpenMP threads ({dt:.1f} s)"}
+    res = {"value": nc * budget_steps / dt, "unit": "cell-updates/s", "cores": oracle.get_threads(),
+           "kind": "oracle", "sample": f"{budget_steps} S2O4 step(s) of the full {nc}-cell mesh, FP64, "
+                                       f"{oracle.get_threads()} OpenMP threads ({dt:.1f} s)"}
+    if H is not None:
+        qo, to, no = o.get_state()
+        vol = o.geometry()[0]
+        names = (("rho", 0), ("rhoU", 1), ("rhoV", 2), ("rhoW", 3), ("rhoE", 4))
+        for prec, key in ((H.HGKS_FP64, "fp64_vs_oracle"), (H.HGKS_FP32_MIXED, "mixed_vs_oracle")):
+            s = H.Solver(H.Mesh(w["xyz"], w["cells"], w["periods"], w.get("bfn"), w.get("bft")), w["q"],
+                         precision=prec, **w["params"])
+            s.step(budget_steps)
+            qg, tg, ng = s.read()
+            s.close()
+            res[key] = {"steps": ng, "time_rel_diff": abs(tg - to) / to,
+                        "max_rel": {k: float(np.abs(qg[:, v] - qo[:, v]).max() / np.abs(qo[:, v]).max())
+                                    for k, v in names},
+                        "l1_rel": {k: float((np.abs(qg[:, v] - qo[:, v]) * vol).sum() /
+                                            (np.abs(qo[:, v]) * vol).sum()) for k, v in names}}
+    return res
 
 
 def run_reference(args, rank, world):
@@ -250,28 +309,18 @@ def mixed_vs_fp64(H, w, stream, K, W, error_steps: int = 20):
     """FP32-mixed throughput on the same workload, and its L1 difference from
     the FP64 path after `error_steps` steps of the same fixed dt from the same
     state."""
-    import torch
-
     nc = len(w["cells"])
-    s = H.Solver(H.Mesh(w["xyz"], w["cells"], w["periods"], w.get("bfn"), w.get("bft")), w["q"],
-                 precision=H.HGKS_FP32_MIXED, stream=stream.cuda_stream, **w["params"])
-    s.step(W)
-    s.sync()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    s.step(K)
-    e1.record(stream)
-    e1.synchronize()
-    ms = e0.elapsed_time(e1)
+    base = H.Mesh(w["xyz"], w["cells"], w["periods"], w.get("bfn"), w.get("bft"))
+    nf, kst = base.n_faces, base.stencil_size
+    s = H.Solver(base.clone(), w["q"], precision=H.HGKS_FP32_MIXED, stream=stream.cuda_stream, **w["params"])
+    ms = timed_steps(s, stream, K, W)
     prof = s.profile(K)
+    s.close()
     # precision: both paths from the initial state with the FP64 path's first dt
     dts = []
     out = {}
     for prec in (H.HGKS_FP64, H.HGKS_FP32_MIXED):
-        t = H.Solver(H.Mesh(w["xyz"], w["cells"], w["periods"], w.get("bfn"), w.get("bft")), w["q"],
-                     precision=prec, **w["params"])
+        t = H.Solver(base.clone(), w["q"], precision=prec, **w["params"])
         if not dts:
             t.step(1)
             dts.append(t.read()[1])
@@ -279,24 +328,87 @@ def mixed_vs_fp64(H, w, stream, K, W, error_steps: int = 20):
         t.step(error_steps, dt_fixed=dts[0])
         out[prec] = t.read()[0]
         t.close()
-    vol = H.Mesh(w["xyz"], w["cells"], w["periods"], w.get("bfn"), w.get("bft")).geometry()[0]
+    vol = base.geometry()[0]
     a, b = out[H.HGKS_FP32_MIXED], out[H.HGKS_FP64]
     l1 = {name: float((np.abs(a[:, v] - b[:, v]) * vol).sum() / (np.abs(b[:, v]) * vol).sum())
           for name, v in (("rho", 0), ("rhoU", 1), ("rhoE", 4))}
     linf = {name: float(np.abs(a[:, v] - b[:, v]).max() / np.abs(b[:, v]).max())
             for name, v in (("rho", 0), ("rhoU", 1), ("rhoE", 4))}
-    s.close()
+    G = 3 if len(w["cells"][0]) == 4 else 4
+    viscous = bool(w["params"].get("mu_ref", 0.0) or w["params"].get("tau_num_c", 0.0))
     res = {"value": nc * K / (ms * 1e-3), "unit": "cell-updates/s", "ms_per_step": ms / K, "dtype": "f32-mixed",
            "kernel_ms_per_step": {"ghost+recon": prof[1], "flux": prof[2], "update": prof[3]},
-           "error_vs_fp64": {"steps": error_steps, "l1_rel": l1, "linf_rel": linf, "dt": dts[0]}}
+           "error_vs_fp64": {"steps": error_steps, "l1_rel": l1, "linf_rel": linf, "dt": dts[0]},
+           "roofline_flux": flux_roofline("mixed", G, viscous, nf, prof[2] / 2.0)}
     if len(w["cells"][0]) == 4 and w["periods"] is not None:
-        kst = H.Mesh(w["xyz"], w["cells"], w["periods"]).stencil_size
         per_launch = recon_rs_bytes_per_cell(kst) * nc
         ach = per_launch / (prof[1] / 2 * 1e-3) / 1e9  # two reconstruction launches per step, no ghosts
         res["roofline_recon"] = {"bound": "hbm", "kernel": "k_recon_rs (binary32)", "achieved": ach,
                                  "peak": HBM_PEAK_GBS, "unit": "GB/s", "frac": ach / HBM_PEAK_GBS,
                                  "bytes_per_launch": per_launch, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
     return res
+
+
+def timed_steps(solver, stream, K, W):
+    """Device time (ms) of K graph-replayed steps after W warm-up steps, CUDA
+    events on the solver's stream."""
+    import torch
+
+    solver.step(W)
+    solver.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    solver.step(K)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def c3_run(H, K, W, error_steps):
+    """The laminar sphere of Section 5.2 on the 1.51M-cell hex shell (6 x 58^2
+    x 75, wall spacing 0.0049, growth 1.08, Ma 0.2535, Re 300): FP64 and
+    FP32-mixed throughput, per-kernel times, the flux roofline of both, and
+    the mixed-vs-FP64 difference after `error_steps` steps of one fixed dt."""
+    import torch
+
+    w = workload("sphere")
+    nc = len(w["cells"])
+    base = H.Mesh(w["xyz"], w["cells"], None, w["bfn"], w["bft"])
+    nf = base.n_faces
+    stream = torch.cuda.Stream()
+    out = {"workload": w["desc"], "cells": nc, "faces": nf}
+    dt0 = None
+    finals = {}
+    for prec, name in ((H.HGKS_FP64, "fp64"), (H.HGKS_FP32_MIXED, "mixed")):
+        s = H.Solver(base.clone(), w["q"], precision=prec, stream=stream.cuda_stream, **w["params"])
+        ms = timed_steps(s, stream, K, W)
+        prof = s.profile(K)
+        s.close()
+        out[name] = {"value": nc * K / (ms * 1e-3), "unit": "cell-updates/s", "ms_per_step": ms / K,
+                     "kernel_ms_per_step": {"finalize": prof[0], "ghost+recon": prof[1], "flux": prof[2],
+                                            "update": prof[3]},
+                     "roofline": flux_roofline(name, 4, True, nf, prof[2] / 2.0)}
+        # both precisions from the initial state with the FP64 path's first dt
+        t = H.Solver(base.clone(), w["q"], precision=prec, **w["params"])
+        if dt0 is None:
+            t.step(1)
+            dt0 = t.read()[1]
+            t.write(w["q"], 0.0)
+        t.step(error_steps, dt_fixed=dt0)
+        finals[name] = t.read()[0]
+        t.close()
+    vol = base.geometry()[0]
+    a, b = finals["mixed"], finals["fp64"]
+    out["mixed"]["error_vs_fp64"] = {
+        "steps": error_steps, "dt": dt0,
+        "l1_rel": {k: float((np.abs(a[:, v] - b[:, v]) * vol).sum() / (np.abs(b[:, v]) * vol).sum())
+                   for k, v in (("rho", 0), ("rhoU", 1), ("rhoE", 4))},
+        "linf_rel": {k: float(np.abs(a[:, v] - b[:, v]).max() / np.abs(b[:, v]).max())
+                     for k, v in (("rho", 0), ("rhoU", 1), ("rhoE", 4))}}
+    out["mixed_speedup"] = out["mixed"]["value"] / out["fp64"]["value"]
+    return out
 
 
 def serve_run(H, small: bool, capacity=None):
@@ -344,7 +456,10 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--workload", default="density48")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-serve", action="store_true", help="skip the small serving run of the default line")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving stream of the default line")
+    ap.add_argument("--serve-small", action="store_true",
+                    help="serve the small stream (48 requests of 5e3..1e5 cells) instead of the full one")
+    ap.add_argument("--no-c3", action="store_true", help="skip the sphere-shell sub-line of the default line")
     ap.add_argument("--error-steps", type=int, default=None,
                     help="steps of the mixed-vs-FP64 comparison (default: the --steps value)")
     ap.add_argument("--serve", action="store_true", help="run the full serving stream (256 requests, up to 2M cells)")
@@ -392,6 +507,7 @@ def main():
     nc = len(w["cells"])
     stream = torch.cuda.Stream()
     mesh = H.Mesh(w["xyz"], w["cells"], w["periods"], w.get("bfn"), w.get("bft"))
+    mesh_nf = mesh.n_faces
     solver = H.Solver(mesh, w["q"], precision=prec, stream=stream.cuda_stream, use_graph=0 if args.no_graph else 1,
                       **w["params"])
     W, K = max(args.warmup, 3), args.steps
@@ -419,19 +535,11 @@ def main():
     # around each group on the solver's stream)
     prof = solver.profile(K)
     flux_ms = prof[2] / 2.0  # two flux launches per step
-    nf = H.Mesh(w["xyz"], w["cells"], w["periods"], w.get("bfn"), w.get("bft")).n_faces
-    roof = {"bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS, "kernel": "k_flux (FP64)",
-            "peak_source": "derived: 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz (measured FMA chain: 1.125 TFLOP/s)",
-            "achieved": None, "frac": None, "traffic": None,
-            "kernel_ms_per_step": {"finalize": prof[0], "ghost+recon": prof[1], "flux": prof[2], "update": prof[3]}}
-    if FP64_FLOPS_PER_FACE_INVISCID and prec == H.HGKS_FP64 and not w["params"] and len(w["cells"][0]) == 4:
-        ach = FP64_FLOPS_PER_FACE_INVISCID * nf / (flux_ms * 1e-3) / 1e12
-        roof["achieved"] = ach
-        roof["frac"] = ach / FP64_PEAK_TFLOPS
-        roof["flop_per_launch"] = FP64_FLOPS_PER_FACE_INVISCID * nf
-        if FP64_FLUX_DRAM_BYTES_PER_FACE:
-            roof["traffic"] = FP64_FLUX_DRAM_BYTES_PER_FACE * nf
-            roof["traffic_source"] = "ncu dram bytes per face of one launch on the 40^3 x 6 mesh, times the faces"
+    nf = mesh_nf
+    G = 3 if len(w["cells"][0]) == 4 else 4
+    viscous = bool(w["params"].get("mu_ref", 0.0) or w["params"].get("tau_num_c", 0.0))
+    roof = flux_roofline(args.precision, G, viscous, nf, flux_ms)
+    roof["kernel_ms_per_step"] = {"finalize": prof[0], "ghost+recon": prof[1], "flux": prof[2], "update": prof[3]}
 
     # ---- end to end through the C ABI with host buffers: per step the state
     # goes host -> device, one step runs, the state comes back
@@ -452,8 +560,11 @@ def main():
     extra = {}
     if args.precision == "fp64":
         extra["mixed"] = mixed_vs_fp64(H, w, stream, K, W, args.error_steps or K)
-    if not args.no_serve:
-        extra["serve"] = serve_run(H, small=True, capacity=extra.get("mixed", {}).get("value"))
+    solo = world == 1
+    if solo and args.workload == "density48" and not args.no_c3:
+        extra["c3"] = c3_run(H, K, W, args.error_steps or K)
+    if solo and not args.no_serve:
+        extra["serve"] = serve_run(H, small=args.serve_small)
 
     if rank == 0:
         line = {"metric": "cell-updates/s", "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": K,
@@ -467,7 +578,7 @@ def main():
                 "clocks": clk.summary()}
         line.update(extra)
         if not args.no_cpu_baseline and world == 1:
-            line["cpu_baseline"] = cpu_baseline(w)
+            line["cpu_baseline"] = cpu_baseline(w, H)
         print(json.dumps(line), flush=True)
     solver.close()
     if dist is not None:
