@@ -41,8 +41,9 @@ sys.path.insert(0, ROOT)
 # Executed operations per unit of the dominant kernels as built, from the ncu
 # operation counts summarised under profiles/ (file named in each entry), and
 # DRAM bytes per unit where a capture measured them.  "sha" is the digest of
-# csrc/hgks_kernels.cu that the counts were taken on: when the source has
-# changed since, the line carries "counts_stale": true and no traffic.
+# the kernel's sources (kernel_source_digest) that the counts were taken on:
+# when they have changed since, the line carries "counts_stale": true and no
+# traffic.
 # Flops: binary64 2 dfma + dadd + dmul (FP64 path), binary32 2 ffma + fadd +
 # fmul (mixed path), per launch divided by the units of the launch.
 ROOF_TABLE = {
@@ -66,12 +67,18 @@ FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12  # SMs x DFMA/clk x 2 flop x max
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x 2 flop x max SM clock
 
 
-def kernel_source_digest() -> str:
+def kernel_source_digest(kernel: str = "k_flux") -> str:
+    """Digest of the sources a kernel is built from (its device header, the
+    shared device helpers and its host launcher)."""
     import hashlib
 
-    p = os.path.join(ROOT, "paper_2407_00656_b300", "csrc", "hgks_kernels.cu")
-    with open(p, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:12]
+    files = {"k_flux": ("hgks_dev_common.cuh", "hgks_dev_flux.cuh", "hgks_flux.cu"),
+             "k_recon_rs": ("hgks_dev_common.cuh", "hgks_dev_recon.cuh", "hgks_recon.cu")}[kernel]
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2407_00656_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
 
 
 def flux_roofline(precision: str, G: int, viscous: bool, faces: int, ms_per_launch: float):

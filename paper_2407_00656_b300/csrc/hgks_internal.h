@@ -143,6 +143,16 @@ struct StepEvents {
   cudaEvent_t ev[8];
 };
 
+// Reconstruction of one stage (hgks_recon.cu): the binary64 stage state Q
+// (FP64 path) or the binary32 records w.Qf (mixed path) into w.coef.
+void launch_recon(const DevMesh& m, const DevParams& p, const DevWork& w, int precision, const double* Q,
+                  cudaStream_t s);
+void prepare_recon(const DevMesh& m, int precision);
+// Face flux of one stage (hgks_flux.cu): w.coef into w.Fs.
+void launch_flux(const DevMesh& m, const DevParams& p, const DevWork& w, int precision, cudaStream_t s);
+// Shared-memory attributes of the persistent kernel (hgks_persist.cu).
+void prepare_persist(const DevMesh& m, int precision);
+
 // Launch one S2O4 step (Algorithm 2) on stream s; precision 0 = FP64, 1 = mixed.
 void launch_step(const DevMesh& m, const DevParams& p, const DevWork& w, int precision, cudaStream_t s,
                  const StepEvents* ev = nullptr);
