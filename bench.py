@@ -47,13 +47,17 @@ sys.path.insert(0, ROOT)
 # Flops: binary64 2 dfma + dadd + dmul (FP64 path), binary32 2 ffma + fadd +
 # fmul (mixed path), per launch divided by the units of the launch.
 ROOF_TABLE = {
-    ("k_flux", "fp64", 3, False): dict(unit="face", flop=4786, dram=469.0, sha="r1-erfcx",
-                                       src="profiles/kernels_fp64_density40.md"),
-    ("k_flux", "fp64", 4, True): dict(unit="face", flop=14149, dram=None, sha="r1-erfcx",
-                                      src="profiles/flux_fp64_viscous_sphere24.md (per Gauss point variant)"),
-    ("k_flux", "mixed", 3, False): dict(unit="face", flop=4437, dram=341.0, sha="r1-erfcx",
-                                        src="profiles/kernels_mixed_density40.md (per Gauss point variant)"),
+    ("k_flux", "fp64", 3, False): dict(unit="face", flop=4786, dram=478.5, sha="79e699e45aa6",
+                                       src="profiles/flux_recon_op_counts.md (48^3 x 6 tets)"),
+    ("k_flux", "fp64", 4, True): dict(unit="face", flop=13020, dram=541.4, sha="79e699e45aa6",
+                                      src="profiles/flux_recon_op_counts.md (6 x 40^2 x 52 hex shell)"),
+    ("k_flux", "mixed", 3, False): dict(unit="face", flop=4368, dram=247.6, sha="79e699e45aa6",
+                                        src="profiles/flux_recon_op_counts.md (48^3 x 6 tets)"),
+    ("k_flux", "mixed", 4, True): dict(unit="face", flop=11739, dram=279.6, sha="79e699e45aa6",
+                                       src="profiles/flux_recon_op_counts.md (6 x 40^2 x 52 hex shell)"),
 }
+# DRAM bytes per cell of k_recon_rs as built, for the traffic of its roofline
+RECON_RS_DRAM = dict(bytes_per_cell=1893.4, sha="f476747f062e", src="profiles/flux_recon_op_counts.md (48^3 x 6 tets)")
 # Algorithmic bytes per cell of one binary32 reconstruction launch (k_recon_rs)
 # on tetrahedra: binary64 pseudo-inverse rows (9K + 3 M KM) x 8 B, sub-stencil
 # positions M KM, stencil indices 4K, second moments and 1/h 7 x 8 B, the
@@ -352,7 +356,11 @@ def mixed_vs_fp64(H, w, stream, K, W, error_steps: int = 20):
         ach = per_launch / (prof[1] / 2 * 1e-3) / 1e9  # two reconstruction launches per step, no ghosts
         res["roofline_recon"] = {"bound": "hbm", "kernel": "k_recon_rs (binary32)", "achieved": ach,
                                  "peak": HBM_PEAK_GBS, "unit": "GB/s", "frac": ach / HBM_PEAK_GBS,
-                                 "bytes_per_launch": per_launch, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+                                 "bytes_per_launch": per_launch, "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+                                 "traffic": None}
+        if RECON_RS_DRAM["sha"] == kernel_source_digest("k_recon_rs") and kst == 14:
+            res["roofline_recon"]["traffic"] = RECON_RS_DRAM["bytes_per_cell"] * nc
+            res["roofline_recon"]["traffic_source"] = RECON_RS_DRAM["src"]
     return res
 
 

@@ -171,6 +171,29 @@ __device__ __forceinline__ void recur(R* m, R U, R h2) {
   for (int n = 0; n + 2 < N; ++n) m[n + 2] = U * m[n + 1] + R(n + 1) * h2 * m[n];
 }
 
+#ifndef HGKS_FAST_F32
+#define HGKS_FAST_F32 1
+#endif
+// Division, exponential and logarithm of the flux.  In binary32 they are the
+// hardware approximations (errors of a few units in the last place, far below
+// the mixed path's error against binary64; 9% off the viscous binary32 flux);
+// HGKS_FAST_F32 = 0 takes the correctly rounded forms.
+template <typename R>
+__device__ __forceinline__ R fdiv(R a, R b) {
+  if constexpr (sizeof(R) == 4 && HGKS_FAST_F32) return __fdividef(a, b);
+  else return a / b;
+}
+template <typename R>
+__device__ __forceinline__ R fexp(R x) {
+  if constexpr (sizeof(R) == 4 && HGKS_FAST_F32) return __expf(x);
+  else return exp(x);
+}
+template <typename R>
+__device__ __forceinline__ R flog(R x) {
+  if constexpr (sizeof(R) == 4 && HGKS_FAST_F32) return __logf(x);
+  else return log(x);
+}
+
 template <typename R>
 struct Prim {
   R rho, U, V, W, lam, h2;  // h2 = 1/(2 lam)
@@ -186,7 +209,7 @@ __device__ __forceinline__ Prim<R> prim_of(const R q[5], R kq, R kqi) {
   Prim<R> p;
   p.rho = q[0];
   const R e2 = q[0] * q[4] - R(0.5) * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-  const R d = R(1) / (q[0] * e2);
+  const R d = fdiv(R(1), q[0] * e2);
   const R ri = e2 * d;
   p.U = q[1] * ri;
   p.V = q[2] * ri;
@@ -209,7 +232,7 @@ __device__ __forceinline__ void moments(const Prim<R>& p, int half, R Kint, Mom<
   } else {
     const R rs = rsqrt(p.lam);
     const R s = R(half) * p.lam * rs * p.U;  // sqrt(lam) U
-    const R ex = exp(-p.lam * p.U * p.U);    // exp(-s^2)
+    const R ex = fexp(-p.lam * p.U * p.U);    // exp(-s^2)
     const R e = ex * R(0.28209479177387814) * rs;  // exp(-lam U^2)/(2 sqrt(pi lam))
     if constexpr (sizeof(R) == 8) {
       // binary64: erfc(-s) from the scaled function erfcx(|s|) =
@@ -245,7 +268,7 @@ template <typename R>
 __device__ __forceinline__ EState<R> estate(const R q[5], R gamma) {
   EState<R> s;
   s.rho = q[0];
-  s.ri = R(1) / q[0];
+  s.ri = fdiv(R(1), q[0]);
   for (int a = 0; a < 3; ++a) { s.m[a] = q[1 + a]; s.u[a] = q[1 + a] * s.ri; }
   s.E = q[4];
   s.gm1 = gamma - R(1);
@@ -383,6 +406,19 @@ __device__ __forceinline__ void phi_jet(const Mom<R>& M, const Prim<R>& pm, R Eh
   out[4] = R(0.5) * (P[0] * (va + vb + vc + v0 * X1) + da + db + dc + d0 * X1 + v0 * dX1);
 }
 
+// The value of Phi / rho = <u^a v^b w^c psi> itself (phi_jet along
+// P = (1, 0, 0, 0, 0), without the derivative terms that vanish there).
+template <int a, int b, int c, typename R>
+__device__ __forceinline__ void phi_val(const Mom<R>& M, const Prim<R>& pm, R Kint, R out[5]) {
+  const R v0 = M.u[a] * M.v[b] * M.w[c];
+  out[0] = v0;
+  out[1] = M.u[a + 1] * M.v[b] * M.w[c];
+  out[2] = M.u[a] * M.v[b + 1] * M.w[c];
+  out[3] = M.u[a] * M.v[b] * M.w[c + 1];
+  const R va = M.u[a + 2] * M.v[b] * M.w[c], vb = M.u[a] * M.v[b + 2] * M.w[c], vc = M.u[a] * M.v[b] * M.w[c + 2];
+  out[4] = R(0.5) * (va + vb + vc + v0 * (Kint * pm.h2));
+}
+
 // X = sum_j rho <u u_j psi a_j>, the spatial-slope term of the
 // non-equilibrium part of Eq. flux for one side (Maxwellian p with moments M
 // over its half line, slopes d[j] of the conservative variables along the
@@ -423,36 +459,71 @@ __device__ __forceinline__ FluxParams<R> flux_params(const DevParams& P) {
   return F;
 }
 
-// Gas-kinetic flux in the local frame (normal = first axis).
-//   ql, qr: conservative states on the two sides of the Gauss point
-//   dl[j], dr[j]: their derivatives along the local axes j = n, t1, t2
-// Output: F^n and dF/dt of Eq. expansion-1 (Section 2.2) for step dt
-// (dt2i = 2/dt).
-template <typename R, bool VISC>
-__device__ void gks_flux(const R ql[5], const R dl[3][5], const R qr[5], const R dr[3][5], R dt, R dt2i,
-                         const FluxParams<R>& P, R F[5], R dF[5]) {
+// Gas-kinetic flux in the local frame (normal = first axis), in two parts so
+// that the two sides stream through one at a time:
+//
+//   side_flux   one side's state q and derivatives d[j] along the local axes
+//               j = n, t1, t2: its half-space part of the interface
+//               equilibrium Q0 and of the slopes dQ0/dn_j, added to q0 and
+//               dq0, and (viscous) its non-equilibrium moment sums, added to
+//               S: S[0] = sum_j rho <u u_j psi a_j> (spatial slopes),
+//               S[1] = rho <u psi> (the initial distribution itself),
+//               S[2] = rho <u A psi> (time slope, rho <A psi> = -sum_j J_j d_j)
+//   eq_flux     the equilibrium part from Q0 and its slopes, the collision
+//               time, and the time integrals that weight the side sums
+//
+// Both sides' non-equilibrium terms carry the same weights, so their sums
+// are formed first and weighted once.  Output: F^n and dF/dt of Eq.
+// expansion-1 (Section 2.2) for step dt (dt2i = 2/dt).
+// FIRST: the side that starts the sums (they are assigned, not added to, so
+// that no addition of zero is spent).
+template <typename R, bool VISC, bool FIRST>
+__device__ __forceinline__ void side_flux(const R q[5], const R d[3][5], int half, const FluxParams<R>& P,
+                                          R q0[5], R dq0[3][5], R S[3][5], R& pside) {
   const R K = P.Kint;
-  const Prim<R> pl = prim_of(ql, P.kq, P.kqi), pr = prim_of(qr, P.kq, P.kqi);
+  const Prim<R> p = prim_of(q, P.kq, P.kqi);
   constexpr int NU = VISC ? 5 : 3;
-  Mom<R> Ml, Mr;
-  R El, Er;
-  moments<NU>(pl, +1, K, Ml, El);
-  moments<NU>(pr, -1, K, Mr, Er);
-
-  // interface equilibrium Q0 = rho_l <psi>^+_l + rho_r <psi>^-_r and its
-  // slopes dQ0/dn_j = int_{u>0} psi a^l_j g_l + int_{u<0} psi a^r_j g_r
-  R q0[5], dq0[3][5];
+  Mom<R> M;
+  R Eh;
+  moments<NU>(p, half, K, M, Eh);
   {
-    R cl[5], dcl[3][5], cr[5], dcr[3][5];
-    half_jet(pl, Ml.u[0], Ml.u[1], El, K, P.kqi, dl, cl, dcl);
-    half_jet(pr, Mr.u[0], Mr.u[1], Er, K, P.kqi, dr, cr, dcr);
+    R c[5], dc[3][5];
+    half_jet(p, M.u[0], M.u[1], Eh, K, P.kqi, d, c, dc);
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
-      q0[i] = cl[i] + cr[i];
+      q0[i] = FIRST ? c[i] : q0[i] + c[i];
 #pragma unroll
-      for (int j = 0; j < 3; ++j) dq0[j][i] = dcl[j][i] + dcr[j][i];
+      for (int j = 0; j < 3; ++j) dq0[j][i] = FIRST ? dc[j][i] : dq0[j][i] + dc[j][i];
     }
   }
+  if constexpr (VISC) {
+    pside = p.rho * p.h2;
+    R X[5];
+    side_terms(p, M, Eh, K, P.kqi, d, X);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) S[0][i] = FIRST ? X[i] : S[0][i] + X[i];
+    R tmp[5], s1[5], s2[5], Pp[5], y[5];
+    const EState<R> st = estate(q, P.gamma);
+    euler_jv<0>(st, d[0], tmp);
+    euler_jv<1>(st, d[1], s1);
+    euler_jv<2>(st, d[2], s2);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) tmp[i] = -(tmp[i] + s1[i] + s2[i]);
+    prim_pert(p, P.kqi, tmp, Pp);
+    phi_jet<1, 0, 0>(M, p, Eh, K, Pp, y);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) S[2][i] = FIRST ? y[i] : S[2][i] + y[i];
+    // rho <u psi>
+    phi_val<1, 0, 0>(M, p, K, y);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) S[1][i] = FIRST ? p.rho * y[i] : fma(p.rho, y[i], S[1][i]);
+  }
+}
+
+template <typename R, bool VISC>
+__device__ __forceinline__ void eq_flux(const R q0[5], const R dq0[3][5], const R S[3][5], R plp, R prp, R dt,
+                                        R dt2i, const FluxParams<R>& P, R F[5], R dF[5]) {
+  const R K = P.Kint;
   // Euler flux of Q0 and the time derivative of Q0 from the compatibility
   // condition <abar.u + Abar> = 0:  dQ0/dt = -sum_j J_j(Q0) dQ0/dn_j
   const EState<R> s0 = estate(q0, P.gamma);
@@ -476,14 +547,14 @@ __device__ void gks_flux(const R ql[5], const R dl[3][5], const R qr[5], const R
     return;
   } else {
     const Prim<R> p0 = prim_of(q0, P.kq, P.kqi);
-    const R plp = pl.rho * pl.h2, prp = pr.rho * pr.h2, p0p = p0.rho * p0.h2;
+    const R p0p = p0.rho * p0.h2;
     // collision time: tau = mu(T0)/p0 + C dt |p_l - p_r|/(p_l + p_r), T = p/rho
     R mu = P.mu_ref;
     // (T0/T_ref)^e as exp(e log(T0/T_ref)): a few units in the last place,
     // for about half the cost of pow
-    if (P.visc_exp != R(0) && mu != R(0)) mu = P.mu_ref * exp(P.visc_exp * log(p0.h2 / P.T_ref));  // T0 = 1/(2 lam0)
+    if (P.visc_exp != R(0) && mu != R(0)) mu = P.mu_ref * fexp(P.visc_exp * flog(fdiv(p0.h2, P.T_ref)));  // T0 = 1/(2 lam0)
     const R sp = plp + prp;
-    const R tau = (mu * sp + P.tau_c * dt * fabs(plp - prp) * p0p) / (p0p * sp);  // one division
+    const R tau = fdiv(mu * sp + P.tau_c * dt * fabs(plp - prp) * p0p, p0p * sp);  // one division
     if (!(tau > R(0))) {
 #pragma unroll
       for (int i = 0; i < 5; ++i) { F[i] = Fe[i]; dF[i] = Ye[i]; }
@@ -493,7 +564,7 @@ __device__ void gks_flux(const R ql[5], const R dl[3][5], const R qr[5], const R
     // dF = 4 (I(dt) - 2 I(dt/2))/dt^2, with h = dt/2, r = tau/h and
     // em = 1 - exp(-h/tau)
     const R r = tau * dt2i;  // dt2i = 1/h
-    const R em = -expm1(R(-1) / r);
+    const R em = -expm1(fdiv(R(-1), r));
     const R g = em * (R(2) + em);  // 3 - 4 e^{-h/tau} + e^{-2h/tau}
     const R C1 = R(1) - R(0.5) * r * g;
     const R C2 = tau * (r * g - (R(2) - em * em));
@@ -505,9 +576,8 @@ __device__ void gks_flux(const R ql[5], const R dl[3][5], const R qr[5], const R
     const R D3 = R(1) - r * r * em * em;
     const R D4 = -D1;
     const R D5 = D2;
-    // F = C1 Fe + C2 X0 + C3 Ye + C4 Nk - C5 (Xl + Xr) - tau C4 Yk, and dF
-    // with D1..D5, accumulated term by term as each term is formed (this
-    // keeps few of them live at once)
+    // F = C1 Fe + C2 X0 + C3 Ye - C5 X + C4 N - tau C4 Y over both sides'
+    // sums S = (X, N, Y), and dF with D1..D5
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
       F[i] = C1 * Fe[i] + C3 * Ye[i];
@@ -536,37 +606,12 @@ __device__ void gks_flux(const R ql[5], const R dl[3][5], const R qr[5], const R
         F[4] += P.prfix * qh;
       }
     }
-    // the initial non-equilibrium distribution of each side: spatial slopes
-    // X, time slope Y = rho <u A psi> with rho <A psi> = -sum_j J_j(q) d_j,
-    // and N = rho <u psi>
-    auto side = [&](const R q[5], const R d[3][5], const Prim<R>& p, const Mom<R>& M, R Eh) {
-      R X[5];
-      side_terms(p, M, Eh, K, P.kqi, d, X);
+    const R tC4 = tau * C4, tD4 = tau * D4;
 #pragma unroll
-      for (int i = 0; i < 5; ++i) {
-        F[i] -= C5 * X[i];
-        dF[i] -= D5 * X[i];
-      }
-      R tmp[5], s1[5], s2[5], Pp[5], y[5], nn[5];
-      const EState<R> st = estate(q, P.gamma);
-      euler_jv<0>(st, d[0], tmp);
-      euler_jv<1>(st, d[1], s1);
-      euler_jv<2>(st, d[2], s2);
-#pragma unroll
-      for (int i = 0; i < 5; ++i) tmp[i] = -(tmp[i] + s1[i] + s2[i]);
-      prim_pert(p, P.kqi, tmp, Pp);
-      phi_jet<1, 0, 0>(M, p, Eh, K, Pp, y);
-      // rho <u psi>: the derivative along P = (1, 0, 0, 0, 0) is the value
-      const R e0[5] = {R(1), R(0), R(0), R(0), R(0)};
-      phi_jet<1, 0, 0>(M, p, Eh, K, e0, nn);
-#pragma unroll
-      for (int i = 0; i < 5; ++i) {
-        F[i] += C4 * (p.rho * nn[i]) - tau * C4 * y[i];
-        dF[i] += D4 * (p.rho * nn[i]) - tau * D4 * y[i];
-      }
-    };
-    side(ql, dl, pl, Ml, El);
-    side(qr, dr, pr, Mr, Er);
+    for (int i = 0; i < 5; ++i) {
+      F[i] += C4 * S[1][i] - C5 * S[0][i] - tC4 * S[2][i];
+      dF[i] += D4 * S[1][i] - D5 * S[0][i] - tD4 * S[2][i];
+    }
   }
 }
 

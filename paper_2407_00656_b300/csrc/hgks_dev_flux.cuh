@@ -27,6 +27,14 @@ __device__ __forceinline__ void eval_poly(const Real* __restrict__ coef, int64_t
   }
 }
 
+// Face geometry in the flux precision: the binary64 array, or its binary32
+// rounding stored with the mesh.
+template <typename Real>
+__device__ __forceinline__ Real geo(const double* __restrict__ a64, const float* __restrict__ a32, int64_t i) {
+  if constexpr (sizeof(Real) == 4) return __ldg(a32 + i);
+  else return a64[i];
+}
+
 // Flux of Gauss point g of face f (Eq. flux at one point of the face
 // quadrature), rotated back to the global frame and oriented from the owner
 // to the neighbour: r[0..4] = F, r[5..9] = dF/dt.  Returns the point's
@@ -40,16 +48,13 @@ __device__ __forceinline__ Real point_flux(const DevMesh& m, const DevParams& P,
   Real n[3], t1[3], t2[3];
   const int gn = G == 3 ? 0 : g;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) n[a] = cvt<Real>(m.fn[(gn * 3 + a) * nf + f]);
+  for (int a = 0; a < 3; ++a) n[a] = geo<Real>(m.fn, m.fn32, (gn * 3 + a) * nf + f);
   frame(n, t1, t2);
   Real d[3];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) d[a] = cvt<Real>(m.fdl[(g * 3 + a) * nf + f]);
-  const Real wgt = cvt<Real>(m.fw[g * nf + f]);
-  Real qv[5], gr[5][3];
-  eval_poly<Real, COH>(coef, own, d, qv, gr);
+  for (int a = 0; a < 3; ++a) d[a] = geo<Real>(m.fdl, m.fdl32, (g * 3 + a) * nf + f);
+  const Real wgt = geo<Real>(m.fw, m.fw32, g * nf + f);
   // local frame: rotate momentum, take derivatives along n, t1, t2
-  Real ql[5], dl[3][5], qr[5], dr[3][5];
   auto rot = [&](const Real x[5], Real y[5]) {
     y[0] = x[0];
     y[1] = x[1] * n[0] + x[2] * n[1] + x[3] * n[2];
@@ -57,7 +62,10 @@ __device__ __forceinline__ Real point_flux(const DevMesh& m, const DevParams& P,
     y[3] = x[1] * t2[0] + x[2] * t2[1] + x[3] * t2[2];
     y[4] = x[4];
   };
-  auto local = [&](const Real q[5], const Real gg[5][3], Real qo[5], Real dd[3][5]) {
+  // the side state at offset d of cell c, in the local frame
+  auto local = [&](int64_t c, Real qo[5], Real dd[3][5]) {
+    Real q[5], gg[5][3];
+    eval_poly<Real, COH>(coef, c, d, q, gg);
     rot(q, qo);
     Real tmp[5];
 #pragma unroll
@@ -70,38 +78,57 @@ __device__ __forceinline__ Real point_flux(const DevMesh& m, const DevParams& P,
     for (int v = 0; v < 5; ++v) tmp[v] = gg[v][0] * t2[0] + gg[v][1] * t2[1] + gg[v][2] * t2[2];
     rot(tmp, dd[2]);
   };
-  local(qv, gr, ql, dl);
-  if (nbr >= 0) {
+  // the two sides one after the other, each folded into the running sums
+  // (the owner's side starts them); with viscosity each side is folded in
+  // before the next is evaluated, which keeps the register footprint down
+  Real q0[5], dq0[3][5], S[3][5], plp = Real(0), prp = Real(0);
+#ifndef FLUX_INVISCID_BOTH_FIRST
+#define FLUX_INVISCID_BOTH_FIRST 0
+#endif
+  constexpr bool both_first = !VISC && FLUX_INVISCID_BOTH_FIRST;
+  Real ql[5], dl[3][5];
+  local(own, ql, dl);
+  if constexpr (!both_first) side_flux<Real, VISC, true>(ql, dl, +1, FP, q0, dq0, S, plp);
+  {
+    Real qr[5], dr[3][5];
+    if (nbr >= 0) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) d[a] = cvt<Real>(m.fdr[(g * 3 + a) * nf + f]);
-    eval_poly<Real, COH>(coef, (int64_t)nbr, d, qv, gr);
-    local(qv, gr, qr, dr);
-  } else if (nbr == -3) {
-    // no-slip adiabatic wall: mirror state, momentum reversed, normal
-    // derivative reflected
+      for (int a = 0; a < 3; ++a) d[a] = geo<Real>(m.fdr, m.fdr32, (g * 3 + a) * nf + f);
+      local((int64_t)nbr, qr, dr);
+    } else {
+      // with viscosity: the owner's side again (cheaper to re-evaluate than
+      // to keep live)
+      if constexpr (!both_first) local(own, ql, dl);
+      if (nbr == -3) {
+        // no-slip adiabatic wall: mirror state, momentum reversed, normal
+        // derivative reflected
 #pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      const Real sg = (v >= 1 && v <= 3) ? Real(-1) : Real(1);
-      qr[v] = sg * ql[v];
-      dr[0][v] = -sg * dl[0][v];
-      dr[1][v] = sg * dl[1][v];
-      dr[2][v] = sg * dl[2][v];
+        for (int v = 0; v < 5; ++v) {
+          const Real sg = (v >= 1 && v <= 3) ? Real(-1) : Real(1);
+          qr[v] = sg * ql[v];
+          dr[0][v] = -sg * dl[0][v];
+          dr[1][v] = sg * dl[1][v];
+          dr[2][v] = sg * dl[2][v];
+        }
+      } else {
+        // Riemann-invariant far field, evaluated in the local frame, zero gradient
+        Real qinf[5], qil[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) qinf[v] = pick<Real>(P.qinf[v], P.f_qinf[v]);
+        rot(qinf, qil);
+        const Real ex[3] = {Real(1), Real(0), Real(0)};
+        farfield(ql, qil, ex, FP.gamma, qr);
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+          for (int v = 0; v < 5; ++v) dr[j][v] = Real(0);
+      }
     }
-  } else {
-    // Riemann-invariant far field, evaluated in the local frame, zero gradient
-    Real qinf[5], qil[5];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) qinf[v] = pick<Real>(P.qinf[v], P.f_qinf[v]);
-    rot(qinf, qil);
-    const Real ex[3] = {Real(1), Real(0), Real(0)};
-    farfield(ql, qil, ex, FP.gamma, qr);
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-#pragma unroll
-      for (int v = 0; v < 5; ++v) dr[j][v] = Real(0);
+    if constexpr (both_first) side_flux<Real, VISC, true>(ql, dl, +1, FP, q0, dq0, S, plp);
+    side_flux<Real, VISC, false>(qr, dr, -1, FP, q0, dq0, S, prp);
   }
   Real Fl[5], Dl[5];
-  gks_flux<Real, VISC>(ql, dl, qr, dr, dt, dt2i, FP, Fl, Dl);
+  eq_flux<Real, VISC>(q0, dq0, S, plp, prp, dt, dt2i, FP, Fl, Dl);
   // back to the global frame
   r[0] = Fl[0];
   r[4] = Fl[4];
@@ -141,10 +168,17 @@ __device__ __forceinline__ void flux_face(const DevMesh& m, const DevParams& P, 
 
 // Face flux, one thread per face: sum over the Gauss points of weight*area
 // times the point flux.  Output: the flux record of each face (store_flux).
-// (binary32 register caps that fit without spilling, measured fastest:
-// inviscid 96 registers, 5 blocks per SM; with viscosity 168, 3 blocks per SM)
+// Binary32 blocks per SM, measured fastest: inviscid 5 (96 registers, no
+// spills; 6 and 7 spill and run 5% and 13% slower), viscous 4 (128 registers,
+// 36 bytes of spills; 2% faster than 3 blocks at 168 registers).
+#ifndef FLUX_INVISC_BLOCKS
+#define FLUX_INVISC_BLOCKS 5
+#endif
+#ifndef FLUX_VISC_BLOCKS
+#define FLUX_VISC_BLOCKS 4
+#endif
 template <typename Real, int G, bool VISC>
-__global__ void __launch_bounds__(kBlock, sizeof(Real) == 4 ? (VISC ? 3 : 5) : 1)
+__global__ void __launch_bounds__(kBlock, sizeof(Real) == 4 ? (VISC ? FLUX_VISC_BLOCKS : FLUX_INVISC_BLOCKS) : 1)
     k_flux(DevMesh m, DevParams P, const Real* __restrict__ coef,
                                                  Real* __restrict__ Fs, const Control* __restrict__ ctl) {
   const int64_t f = (int64_t)blockIdx.x * kBlock + threadIdx.x;

@@ -112,6 +112,13 @@ __global__ void __launch_bounds__(kBlock) k_update2(DevMesh m, DevParams P, cons
   member_min_to(m, ctl, dt != 0.0 ? mid : -1, bound);
 }
 
+// Binary32 rounding of a binary64 array (cvt<float>, as the binary32 kernels
+// round the geometry they read).
+__global__ void k_round32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (i < n) b[i] = cvt<float>(a[i]);
+}
+
 // Binary32 copy of the state (mixed precision).
 // Caller order and layout ([n][5], member-local index perm[c]) to the internal
 // structure-of-arrays order of cells coff .. coff+n-1, and back.

@@ -37,6 +37,12 @@ struct DevMesh {
   const double* fdr;      // [3G][nf]
   const double* fn;       // [3G][nf]
   const double* fw;       // [G][nf]
+  // binary32 roundings of fdl, fdr, fn and fw (as cvt<float> rounds them),
+  // read by the binary32 flux instead of converting on every launch
+  const float* fdl32;     // [3G][nf]
+  const float* fdr32;     // [3G][nf]
+  const float* fn32;      // [3G][nf]
+  const float* fw32;      // [G][nf]
 };
 
 // Physical and numerical parameters as the kernels use them.
@@ -171,6 +177,9 @@ void launch_reset(const DevMesh& m, const DevParams& p, const DevWork& w, int pr
 // of Q ([5][nce]).  `in` and `out` are device buffers.
 void launch_state_in(const DevMesh& m, const double* in, int64_t coff, int64_t n, double* Q, cudaStream_t s);
 void launch_state_out(const DevMesh& m, const double* Q, int64_t coff, int64_t n, double* out, cudaStream_t s);
+// Fill the binary32 face geometry (fdl32, fdr32, fn32, fw32) of a device
+// mesh from its binary64 arrays.
+void launch_face32(const DevMesh& m, cudaStream_t s);
 // L and dL/dt of the current state for step dt into Qs[0:5] and R (as L) -- test path.
 void launch_operator(const DevMesh& m, const DevParams& p, const DevWork& w, int precision, double dt,
                      double* L, double* dL, cudaStream_t s);

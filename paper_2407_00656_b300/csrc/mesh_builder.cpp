@@ -824,6 +824,7 @@ int64_t mesh_static_bytes(const HostMesh& m, int nmesh) {
   b += al(4 * ng) * 2 + al(8 * 3 * ng);        // ghosts
   b += al(4 * nf) * 2;                         // fown, fnbr
   b += al(8 * (int64_t)m.G * 3 * nf) * 3 + al(8 * (int64_t)m.G * nf);  // fdl fdr fn fw
+  b += al(4 * (int64_t)m.G * 3 * nf) * 3 + al(4 * (int64_t)m.G * nf);  // their binary32 roundings
   if (nmesh > 1) b += al(4 * nc);              // member of each cell
   return b + 256;
 }
