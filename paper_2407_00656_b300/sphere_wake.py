@@ -91,6 +91,14 @@ class ShellView:
         self.wall = np.nonzero(on_wall[cells].sum(axis=1) >= 4)[0]
         if len(self.wall) == 0:
             raise ValueError("no cell has a face on the sphere r = r_wall")
+        # the second layer: cells with a whole face on the outer face of the
+        # wall layer
+        outer = np.zeros(len(xyz), dtype=bool)
+        wn = cells[self.wall].ravel()
+        outer[wn[~on_wall[wn]]] = True
+        in_wall = np.zeros(len(cells), dtype=bool)
+        in_wall[self.wall] = True
+        self.layer2 = np.nonzero((outer[cells].sum(axis=1) >= 4) & ~in_wall)[0]
         # angular mesh spacing: a cubed sphere has 6 n^2 cells per layer over
         # the four quarter-circles of each great circle
         n_est = math.sqrt(len(self.wall) / 6.0)
@@ -115,32 +123,37 @@ class ShellView:
         """Wall-layer cells around the front stagnation point."""
         return self._ring(self.phi, self.wall)
 
-    def meridional_velocity(self, u):
-        """Velocity of the wall-layer cells along e_phi, the unit vector of
-        increasing polar angle from the front pole (downstream along the wall)."""
-        c = self.c[self.wall]
-        rhat = c / self.r[self.wall][:, None]
-        cosf = np.cos(self.phi[self.wall])
-        sinf = np.maximum(np.sin(self.phi[self.wall]), 1e-300)
+    def meridional_velocity(self, u, cells=None):
+        """Velocity of the wall-layer cells (or of ``cells``) along e_phi, the
+        unit vector of increasing polar angle from the front pole (downstream
+        along the wall)."""
+        sel = self.wall if cells is None else cells
+        c = self.c[sel]
+        rhat = c / self.r[sel][:, None]
+        cosf = np.cos(self.phi[sel])
+        sinf = np.maximum(np.sin(self.phi[sel]), 1e-300)
         front = np.array([-1.0, 0.0, 0.0])
         e_phi = (cosf[:, None] * rhat - front[None, :]) / sinf[:, None]
-        return (u[self.wall] * e_phi).sum(axis=1)
+        return (u[sel] * e_phi).sum(axis=1)
 
 
-def separation_angle(view: ShellView, q, bin_deg: float | None = None, skip_deg: float = 10.0) -> float:
+def separation_angle(view: ShellView, q, bin_deg: float | None = None, skip_deg: float = 10.0,
+                     layer: int = 1) -> float:
     """Separation angle in degrees from the front stagnation point, or NaN
     when the flow stays attached.
 
-    The wall-layer cells are binned by polar angle (bins one mesh spacing
-    wide by default) and the meridional velocity averaged in each bin.  The
-    result is the first change of sign from positive to negative, scanning
-    from the front, past ``skip_deg`` (where the velocity vanishes at the
-    stagnation point), linearly interpolated between the mean polar angles of
-    the cells of the two bins.
+    The cells of the first (or, ``layer`` = 2, the second) layer on the wall
+    are binned by polar angle (bins one mesh spacing wide by default) and the
+    meridional velocity averaged in each bin.  The result is the first change
+    of sign from positive to negative, scanning from the front, past
+    ``skip_deg`` (where the velocity vanishes at the stagnation point),
+    linearly interpolated between the mean polar angles of the cells of the
+    two bins.
     """
     _, u, _ = primitives(q)
-    ut = view.meridional_velocity(u)
-    phi = view.phi[view.wall]
+    sel = view.wall if layer == 1 else view.layer2
+    ut = view.meridional_velocity(u, sel)
+    phi = view.phi[sel]
     width = math.radians(bin_deg) if bin_deg else view.spacing
     nb = max(1, int(round(math.pi / width)))
     k = np.minimum((phi / math.pi * nb).astype(np.int64), nb - 1)
@@ -265,6 +278,8 @@ def march(mach: float, re: float, n: int = 24, n_r: int | None = None, r_far: fl
         rho, u, p = primitives(q)
         front = view.front_cells()
         rec = dict(t=t, steps=steps, L=wake_length(view, q), theta=separation_angle(view, q),
+                   theta_bin2=separation_angle(view, q, bin_deg=2.0 * math.degrees(view.spacing)),
+                   theta_layer2=separation_angle(view, q, layer=2),
                    p_stag=float(p[front].mean()), rho_stag=float(rho[front].mean()),
                    standoff=shock_standoff(view, q) if mach > 1.0 else None,
                    max_mach=float(np.sqrt((u * u).sum(axis=1) * rho / (GAMMA * p)).max()),
@@ -284,7 +299,8 @@ def march(mach: float, re: float, n: int = 24, n_r: int | None = None, r_far: fl
     summary = dict(mach=mach, re=re, cells=len(cells), shell=f"6x{n}^2x{n_r}", growth=growth, r_far=r_far,
                    first_spacing=float(r_far - 0.5) * (growth - 1.0) / (growth ** n_r - 1.0),
                    precision="mixed" if precision == 1 else "fp64", t=t, steps=steps,
-                   L=records[-1]["L"], theta=records[-1]["theta"], p_stag=records[-1]["p_stag"],
+                   L=records[-1]["L"], theta=records[-1]["theta"], theta_bin2=records[-1]["theta_bin2"],
+                   theta_layer2=records[-1]["theta_layer2"], p_stag=records[-1]["p_stag"],
                    p_stag_pitot=pitot_pressure(mach), rho_stag=records[-1]["rho_stag"],
                    rho_stag_pitot=stagnation_density(mach), standoff=records[-1]["standoff"],
                    standoff_billig=billig_standoff(mach) if mach > 1.0 else None,

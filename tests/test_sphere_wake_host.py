@@ -46,6 +46,9 @@ def test_view_finds_wall_layer_and_axis_rings(shell):
     assert len(ax) == 4 * 24
     assert np.all(v.c[ax, 0] > 0)
     assert len(v.front_cells()) == 4
+    # the second layer: one cell above each wall cell, none on the wall
+    assert len(v.layer2) == len(v.wall) and not set(v.layer2) & set(v.wall)
+    assert np.all(v.r[v.layer2] > v.r[v.wall].max())
 
 
 @pytest.mark.parametrize("theta_deg", [118.0, 128.4, 136.8, 150.0])
@@ -67,6 +70,11 @@ def test_separation_angle_of_a_field_with_known_reversal(shell, theta_deg):
     q = state_from(np.full(len(c), 1.0), u, np.full(len(c), 1 / 1.4))
     got = W.separation_angle(v, q)
     assert abs(got - theta_deg) < 0.6, got
+    # the sensitivity variants read the same field: twice as wide bins, and
+    # the second cell layer on the wall
+    wide = 2 * math.degrees(v.spacing)  # 15 degrees on this coarse shell
+    assert abs(W.separation_angle(v, q, bin_deg=wide) - theta_deg) < 0.2 * wide
+    assert abs(W.separation_angle(v, q, layer=2) - theta_deg) < 0.6
 
 
 def test_separation_angle_is_nan_for_attached_flow(shell):
