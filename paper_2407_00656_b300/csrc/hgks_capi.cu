@@ -152,6 +152,7 @@ void hgks_params_default(hgks_params* p) {
 const char* hgks_last_error(void) { return g_err.c_str(); }
 
 int hgks_mesh_create(const hgks_mesh_desc* d, hgks_mesh** out) {
+  hgks::Range range("hgks_mesh_create");
   if (!d || !out) return fail(HGKS_EINVAL, "NULL argument");
   *out = nullptr;
   if (d->cell_type != HGKS_TET4 && d->cell_type != HGKS_HEX8) return fail(HGKS_EINVAL, "cell_type must be 4 or 8");
@@ -608,12 +609,14 @@ int read_flags(hgks_solver* s, int only, hgks::Control* first) {
 extern "C" {
 
 int hgks_init(hgks_mesh* mesh, const hgks_params* params, const double* q0, hgks_solver** out) {
+  hgks::Range range("hgks_init");
   if (!mesh || !out || !q0) return fail(HGKS_EINVAL, "NULL argument");
   return create_solver(&mesh, 1, params, &q0, out);
 }
 
 int hgks_batch_init(hgks_mesh* const* meshes, int n, const hgks_params* params, const double* const* q0,
                     hgks_solver** out) {
+  hgks::Range range("hgks_batch_init");
   if (!meshes || !q0 || !out || n <= 0) return fail(HGKS_EINVAL, "bad argument");
   for (int i = 0; i < n; ++i)
     if (!meshes[i] || !q0[i]) return fail(HGKS_EINVAL, "NULL member mesh or state");
@@ -623,6 +626,7 @@ int hgks_batch_init(hgks_mesh* const* meshes, int n, const hgks_params* params, 
 int hgks_members(const hgks_solver* s) { return s ? (int)s->members().size() : -1; }
 
 int hgks_member_write(hgks_solver* s, int member, const double* q, double t) {
+  hgks::Range range("hgks_write");
   if (!s || !q) return fail(HGKS_EINVAL, "NULL argument");
   if (member < 0 || member >= (int)s->members().size()) return fail(HGKS_EINVAL, "member out of range");
   // the caller's states go into Q* (scratch between steps; ordered after the
@@ -641,6 +645,7 @@ int hgks_member_write(hgks_solver* s, int member, const double* q, double t) {
 int hgks_write(hgks_solver* s, const double* q, double t) { return hgks_member_write(s, 0, q, t); }
 
 int hgks_step(hgks_solver* s, int n_steps, double t_end, double dt_fixed) {
+  hgks::Range range("hgks_step");
   if (!s) return fail(HGKS_EINVAL, "NULL solver");
   if (n_steps < 0) return fail(HGKS_EINVAL, "n_steps must be >= 0");
   if (n_steps == 0) return HGKS_OK;
@@ -682,6 +687,7 @@ int hgks_query(hgks_solver* s) {
 }
 
 int hgks_sync(hgks_solver* s) {
+  hgks::Range range("hgks_sync");
   if (!s) return fail(HGKS_EINVAL, "NULL solver");
   HGKS_CUDA(cudaStreamSynchronize(s->stream), "synchronising");
   HGKS_CUDA(cudaGetLastError(), "synchronising");
@@ -708,10 +714,12 @@ int hgks_member_read(hgks_solver* s, int member, double* q_out, double* t_out, i
 }
 
 int hgks_read(hgks_solver* s, double* q_out, double* t_out, int64_t* steps_out) {
+  hgks::Range range("hgks_read");
   return hgks_member_read(s, 0, q_out, t_out, steps_out);
 }
 
 int hgks_stage_operator(hgks_solver* s, double dt, double* L_out, double* dL_out) {
+  hgks::Range range("hgks_stage_operator");
   if (!s || !L_out || !dL_out) return fail(HGKS_EINVAL, "NULL argument");
   if (!(dt > 0.0)) return fail(HGKS_EINVAL, "dt must be positive");
   if (s->members().size() != 1) return fail(HGKS_EINVAL, "the stage operator is defined for single-mesh solvers");
@@ -729,6 +737,7 @@ int hgks_stage_operator(hgks_solver* s, double dt, double* L_out, double* dL_out
 }
 
 int hgks_profile(hgks_solver* s, int n_steps, double t_end, double dt_fixed, double* ms_out) {
+  hgks::Range range("hgks_profile");
   if (!s || !ms_out || n_steps <= 0) return fail(HGKS_EINVAL, "bad argument");
   hgks::StepEvents ev;
   for (int i = 0; i < 8; ++i) HGKS_CUDA(cudaEventCreate(&ev.ev[i]), "creating events");
@@ -787,6 +796,7 @@ int hgks_tuning(const hgks_solver* s, int* flux_variant, int* recon_variant) {
 }
 
 void hgks_destroy(hgks_solver* s) {
+  hgks::Range range("hgks_destroy");
   if (!s) return;
   if (s->stream) cudaStreamSynchronize(s->stream);
   if (s->graph) cudaGraphExecDestroy(s->graph);
@@ -798,6 +808,7 @@ void hgks_destroy(hgks_solver* s) {
 }
 
 int hgks_dmesh_create(const hgks_mesh* mesh, void* stream, hgks_dmesh** out) {
+  hgks::Range range("hgks_dmesh_create");
   if (!mesh || !out) return fail(HGKS_EINVAL, "NULL argument");
   *out = nullptr;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -839,6 +850,7 @@ int64_t hgks_dmesh_info(const hgks_dmesh* d, int what) {
 }
 
 int hgks_init_shared(hgks_dmesh* dmesh, const hgks_params* params, const double* q0, hgks_solver** out) {
+  hgks::Range range("hgks_init_shared");
   if (!dmesh || !out || !q0) return fail(HGKS_EINVAL, "NULL argument");
   *out = nullptr;
   int rc = hgks::check_params(params);

@@ -6,6 +6,7 @@
 #include <string>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "hgks.h"
 
@@ -126,6 +127,15 @@ struct DevWork {
   void* Fs;       // [nf][kFluxRec] face flux sums: F (5) then dF/dt (5) (double or float)
   Control* ctl;   // [nmesh] one control block per member mesh
   GridBar* bar;   // barrier of the persistent step kernel
+};
+
+// NVTX range over a scope: entry points and step phases show up by name on a
+// profiler's timeline (no cost without a profiler attached).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
 };
 
 // Message returned by hgks_last_error() on this thread.

@@ -24,24 +24,30 @@ void stage_pair(const DevMesh& m, const DevParams& p, const DevWork& w, bool mix
   const unsigned nbc = blocks(m.nc);
   float* Qf = mixed ? w.Qf : nullptr;
   auto mark = [&](int i) { if (ev) cudaEventRecord(ev->ev[i], s); };
-  // stage 1 on Q^n
-  if (m.ng) k_ghost<<<blocks(m.ng), kBlock, 0, s>>>(m, p, w.Q, Qf, w.ctl);
-  launch_recon(m, p, w, mixed ? 1 : 0, w.Q, s);
-  mark(2);
-  launch_flux(m, p, w, mixed ? 1 : 0, s);
-  mark(3);
-  if (m.nfc == 4) k_update1<Real, 4><<<nbc, kBlock, 0, s>>>(m, Fs, w.Q, w.Qs, w.R, Qf, w.ctl);
-  else k_update1<Real, 6><<<nbc, kBlock, 0, s>>>(m, Fs, w.Q, w.Qs, w.R, Qf, w.ctl);
-  mark(4);
-  // stage 2 on Q*
-  if (m.ng) k_ghost<<<blocks(m.ng), kBlock, 0, s>>>(m, p, w.Qs, Qf, w.ctl);
-  launch_recon(m, p, w, mixed ? 1 : 0, w.Qs, s);
-  mark(5);
-  launch_flux(m, p, w, mixed ? 1 : 0, s);
-  mark(6);
-  if (m.nfc == 4) k_update2<Real, 4><<<nbc, kBlock, 0, s>>>(m, p, Fs, w.Q, w.R, Qf, w.ctl);
-  else k_update2<Real, 6><<<nbc, kBlock, 0, s>>>(m, p, Fs, w.Q, w.R, Qf, w.ctl);
-  mark(7);
+  {
+    // stage 1 on Q^n
+    Range r1("stage 1: ghosts, reconstruction, flux, update");
+    if (m.ng) k_ghost<<<blocks(m.ng), kBlock, 0, s>>>(m, p, w.Q, Qf, w.ctl);
+    launch_recon(m, p, w, mixed ? 1 : 0, w.Q, s);
+    mark(2);
+    launch_flux(m, p, w, mixed ? 1 : 0, s);
+    mark(3);
+    if (m.nfc == 4) k_update1<Real, 4><<<nbc, kBlock, 0, s>>>(m, Fs, w.Q, w.Qs, w.R, Qf, w.ctl);
+    else k_update1<Real, 6><<<nbc, kBlock, 0, s>>>(m, Fs, w.Q, w.Qs, w.R, Qf, w.ctl);
+    mark(4);
+  }
+  {
+    // stage 2 on Q*
+    Range r2("stage 2: ghosts, reconstruction, flux, update");
+    if (m.ng) k_ghost<<<blocks(m.ng), kBlock, 0, s>>>(m, p, w.Qs, Qf, w.ctl);
+    launch_recon(m, p, w, mixed ? 1 : 0, w.Qs, s);
+    mark(5);
+    launch_flux(m, p, w, mixed ? 1 : 0, s);
+    mark(6);
+    if (m.nfc == 4) k_update2<Real, 4><<<nbc, kBlock, 0, s>>>(m, p, Fs, w.Q, w.R, Qf, w.ctl);
+    else k_update2<Real, 6><<<nbc, kBlock, 0, s>>>(m, p, Fs, w.Q, w.R, Qf, w.ctl);
+    mark(7);
+  }
 }
 
 }  // namespace
@@ -102,6 +108,7 @@ void launch_reset(const DevMesh& m, const DevParams& p, const DevWork& w, int pr
 
 void launch_step(const DevMesh& m, const DevParams& p, const DevWork& w, int precision, cudaStream_t s,
                  const StepEvents* ev) {
+  Range range("S2O4 step");
   if (ev) cudaEventRecord(ev->ev[0], s);
   k_finalize<<<(m.nmesh + 127) / 128, 128, 0, s>>>(w.ctl, m.nmesh, p.cfl);
   if (ev) cudaEventRecord(ev->ev[1], s);
