@@ -353,6 +353,82 @@ struct ReconSmemF {
   static constexpr int blocks = best;
 };
 
+// The least-squares polynomials of one (variable, cell) thread from a
+// binary32 tile of inverse rows ([rows][kRC]) and the block's neighbour
+// states snbr ([5][K][kRC]) less the cell's own qv: the quadratic (a, 9
+// coefficients from tile rows 0 .. 9K-1) and the linear ones (b, 3 per
+// sub-stencil from rows LB .. LB + 3 M KM - 1, members at positions ssub).
+// The operation order is that of k_recon.  On hexahedra, pairs of output
+// rows advance together in packed binary32 FMAs (two independent
+// round-to-nearest FMAs per instruction: the same results); measured 8%
+// faster there and 5% slower on tetrahedra.
+template <int K, int M>
+__device__ __forceinline__ void rs_quadratic(const float* tile, const float* snbr, float qv, int v, int lane,
+                                             float a[9]) {
+  auto row = [&](int r) -> float { return tile[r * kRC + lane]; };
+  float dq[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) dq[k] = snbr[(v * K + k) * kRC + lane] - qv;
+  if constexpr (M == 8) {
+    float2 dq2[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) dq2[k] = make_float2(dq[k], dq[k]);
+#pragma unroll
+    for (int d = 0; d < 8; d += 2) {
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc = __ffma2_rn(make_float2(row(d * K + k), row((d + 1) * K + k)), dq2[k], acc);
+      a[d] = acc.x;
+      a[d + 1] = acc.y;
+    }
+    float sacc = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) sacc = fmaf(row(8 * K + k), dq[k], sacc);
+    a[8] = sacc;
+  } else {
+#pragma unroll
+    for (int d = 0; d < 9; ++d) {
+      float sacc = 0.f;
+#pragma unroll
+      for (int k = 0; k < K; ++k) sacc += row(d * K + k) * dq[k];
+      a[d] = sacc;
+    }
+  }
+}
+
+template <int K, int M, int KM, int LB>
+__device__ __forceinline__ void rs_linear(const float* tile, const float* snbr, const uint8_t* ssub, float qv, int v,
+                                          int lane, float b[M][3]) {
+  auto row = [&](int r) -> float { return tile[r * kRC + lane]; };
+#pragma unroll
+  for (int s = 0; s < M; ++s) {
+    float x[KM];
+#pragma unroll
+    for (int r = 0; r < KM; ++r) x[r] = snbr[(v * K + ssub[(s * KM + r) * kRC + lane]) * kRC + lane] - qv;
+    if constexpr (M == 8) {
+      float2 acc = make_float2(0.f, 0.f);
+      float acc2 = 0.f;
+#pragma unroll
+      for (int r = 0; r < KM; ++r) {
+        acc = __ffma2_rn(make_float2(row(LB + (s * 3) * KM + r), row(LB + (s * 3 + 1) * KM + r)),
+                         make_float2(x[r], x[r]), acc);
+        acc2 = fmaf(row(LB + (s * 3 + 2) * KM + r), x[r], acc2);
+      }
+      b[s][0] = acc.x;
+      b[s][1] = acc.y;
+      b[s][2] = acc2;
+    } else {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        float acc = 0.f;
+#pragma unroll
+        for (int r = 0; r < KM; ++r) acc += row(LB + (s * 3 + d) * KM + r) * x[r];
+        b[s][d] = acc;
+      }
+    }
+  }
+}
+
 template <int K, int M, int KM, bool COH = false>
 __device__ __forceinline__ void recon_rs_block(const DevMesh& m, const DevParams& P, const float* __restrict__ Qf,
                                                float* __restrict__ coef, int64_t c0, unsigned char* smem_raw) {
@@ -479,45 +555,14 @@ __device__ __forceinline__ void recon_rs_block(const DevMesh& m, const DevParams
       if (live) sgeo[r * kRC + lane] = cvt<float>(r < 6 ? m.mom[(int64_t)r * nc + c0 + lane] : m.hinv[c0 + lane]);
   __syncthreads();
   float res[10];
-  // least-squares polynomials (the operation order of k_recon).  On
-  // hexahedra, pairs of output rows advance together in packed binary32 FMAs
-  // (two independent round-to-nearest FMAs per instruction: the same
-  // results); measured 8% faster there and 5% slower on tetrahedra.
-  auto row = [&](int r) -> float { return tile[r * kRC + lane]; };
+  // least-squares polynomials (rs_quadratic, rs_linear)
   constexpr int LB = S::phased ? 0 : R0;  // tile row of the first linear row
   float a[9];
   float b[M][3];
   float qv = 0.f;
   if (live) {
     qv = S::lean ? qown : sown[v * kRC + lane];
-    float dq[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) dq[k] = snbr[(v * K + k) * kRC + lane] - qv;
-    if constexpr (M == 8) {
-      float2 dq2[K];
-#pragma unroll
-      for (int k = 0; k < K; ++k) dq2[k] = make_float2(dq[k], dq[k]);
-#pragma unroll
-      for (int d = 0; d < 8; d += 2) {
-        float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int k = 0; k < K; ++k) acc = __ffma2_rn(make_float2(row(d * K + k), row((d + 1) * K + k)), dq2[k], acc);
-        a[d] = acc.x;
-        a[d + 1] = acc.y;
-      }
-      float sacc = 0.f;
-#pragma unroll
-      for (int k = 0; k < K; ++k) sacc = fmaf(row(8 * K + k), dq[k], sacc);
-      a[8] = sacc;
-    } else {
-#pragma unroll
-      for (int d = 0; d < 9; ++d) {
-        float sacc = 0.f;
-#pragma unroll
-        for (int k = 0; k < K; ++k) sacc += row(d * K + k) * dq[k];
-        a[d] = sacc;
-      }
-    }
+    rs_quadratic<K, M>(tile, snbr, qv, v, lane, a);
   }
   if constexpr (S::phased) {
     __syncthreads();  // every warp has read its quadratic rows
@@ -525,33 +570,7 @@ __device__ __forceinline__ void recon_rs_block(const DevMesh& m, const DevParams
     __syncthreads();
   }
   if (live) {
-#pragma unroll
-    for (int s = 0; s < M; ++s) {
-      float x[KM];
-#pragma unroll
-      for (int r = 0; r < KM; ++r) x[r] = snbr[(v * K + ssub[(s * KM + r) * kRC + lane]) * kRC + lane] - qv;
-      if constexpr (M == 8) {
-        float2 acc = make_float2(0.f, 0.f);
-        float acc2 = 0.f;
-#pragma unroll
-        for (int r = 0; r < KM; ++r) {
-          acc = __ffma2_rn(make_float2(row(LB + (s * 3) * KM + r), row(LB + (s * 3 + 1) * KM + r)),
-                           make_float2(x[r], x[r]), acc);
-          acc2 = fmaf(row(LB + (s * 3 + 2) * KM + r), x[r], acc2);
-        }
-        b[s][0] = acc.x;
-        b[s][1] = acc.y;
-        b[s][2] = acc2;
-      } else {
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          float acc = 0.f;
-#pragma unroll
-          for (int r = 0; r < KM; ++r) acc += row(LB + (s * 3 + d) * KM + r) * x[r];
-          b[s][d] = acc;
-        }
-      }
-    }
+    rs_linear<K, M, KM, LB>(tile, snbr, ssub, qv, v, lane, b);
     float mi[6];
 #pragma unroll
     for (int q = 0; q < 6; ++q) mi[q] = S::lean ? gl[q] : sgeo[q * kRC + lane];
