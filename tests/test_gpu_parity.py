@@ -234,3 +234,47 @@ def test_periodic_jittered_hexahedra_stage_operator_and_steps(kw):
     assert n == no == 3 and abs(t - to) <= 1e-15 * to
     assert relerr(qg, qo) < TOL
     s.close()
+
+
+def test_full_size_sphere_shell_one_step():
+    """The 1.51M-cell hex shell of the bench's sphere line (6 x 58^2 x 75,
+    Ma 0.2535, Re 300, power-law viscosity, numerical collision time, wall and
+    far field), from the free stream with smooth seeded perturbations of a
+    few percent: one FP64 step against the oracle, every cell; the mixed
+    path's step within its L1 bound."""
+    import os
+
+    xyz, cells, bfn, bft = I.sphere_shell(58, 75, seed=0)
+    qinf = I.free_stream(0.2535)
+    cen = xyz[cells].mean(axis=1)
+    rng = np.random.default_rng(3)
+    pert = np.zeros((len(cells), 3))
+    for j in range(3):
+        for _ in range(3):
+            k = rng.normal(size=3) * 0.6
+            pert[:, j] += np.sin(cen @ k + rng.uniform(0, 2 * np.pi))
+    rho = 1.0 + 0.02 * pert[:, 0]
+    u = np.stack([0.2535 * (1 + 0.05 * pert[:, 1]), 0.01 * pert[:, 2], np.zeros(len(cells))], axis=1)
+    p = (1 + 0.02 * pert[:, 2]) / 1.4
+    q = np.empty((len(cells), 5))
+    q[:, 0] = rho
+    q[:, 1:4] = rho[:, None] * u
+    q[:, 4] = p / 0.4 + 0.5 * rho * (u * u).sum(axis=1)
+    params = dict(qinf=qinf, mu_ref=0.2535 / 300, Pr=0.72, visc_exp=0.7, T_ref=1 / 1.4, tau_c=1.0)
+    oracle.set_threads(os.cpu_count() or 8)
+    s, o = both(xyz, cells, None, bfn, bft, q=q, **params)
+    s.step(1)
+    o.step(1)
+    qg, t, n = s.read()
+    qo, to, no = o.get_state()
+    s.close()
+    assert n == no == 1 and abs(t - to) <= 1e-15 * to
+    assert relerr(qg, qo) < TOL
+    m = H.Solver(H.Mesh(xyz, cells, None, bfn, bft), q, precision=H.HGKS_FP32_MIXED,
+                 **{_hkey(k): v for k, v in params.items()})
+    m.step(1, dt_fixed=t)
+    qm = m.read()[0]
+    m.close()
+    vol = o.geometry()[0]
+    for v in (0, 1, 4):
+        assert (np.abs(qm[:, v] - qo[:, v]) * vol).sum() / (np.abs(qo[:, v]) * vol).sum() < 1e-5
