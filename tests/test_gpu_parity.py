@@ -268,7 +268,9 @@ def test_full_size_sphere_shell_one_step():
     qg, t, n = s.read()
     qo, to, no = o.get_state()
     s.close()
-    assert n == no == 1 and abs(t - to) <= 1e-15 * to
+    # the step is the viscous bound rho h^2/(2 mu) with mu from the power law,
+    # whose pow() the host and device libraries round a few units apart
+    assert n == no == 1 and abs(t - to) <= 1e-13 * to
     assert relerr(qg, qo) < TOL
     m = H.Solver(H.Mesh(xyz, cells, None, bfn, bft), q, precision=H.HGKS_FP32_MIXED,
                  **{_hkey(k): v for k, v in params.items()})
