@@ -462,7 +462,11 @@ __device__ __forceinline__ void recon_rs_block(const DevMesh& m, const DevParams
   // row counts are compile-time constants, so only the tail row is guarded.
   constexpr int R0 = 9 * K, R1 = M * 3 * KM;  // rows of pinv0 and pinvm
   constexpr int J0 = R0 / 5, T0 = R0 - 5 * J0, J1 = R1 / 5, T1 = R1 - 5 * J1;
-  constexpr int B = 12;  // rows per batch of loads (8: 5% slower on tetrahedra, 16: slower on hexahedra)
+  // rows per batch of loads, measured: 12 in the tile layouts (8 is 5%
+  // slower on tetrahedra, 16 slower on hexahedra); 8 in the lean layout,
+  // whose register-held own state and geometry leave less room (12 took the
+  // K = 26 hybrid shell from 2.52 to 4.58 ms per step)
+  constexpr int B = S::lean ? 8 : 12;
   static_assert(J0 >= B, "the first batch is a full one");
   constexpr int RS = 5 * kRC;  // shared-memory stride between a thread's rows
   const int64_t step = 5 * ncp;
