@@ -306,3 +306,33 @@ def test_six_million_tets_free_stream_and_conservation():
         tot = (q * vol[:, None]).sum(axis=0)
         assert np.abs(q - wave).max() > 1e-4
         assert np.all(np.abs(tot - tot0) <= ctol * np.abs(tot0).max()), (tot - tot0, prec)
+
+
+@pytest.mark.parametrize("mesh", ["hex1", "hex2", "tet1", "tet2"])
+def test_tiny_periodic_meshes_whose_stencils_hold_periodic_images(mesh):
+    """Degenerate periodic meshes: one or two lattice cubes, so every stencil
+    wraps around the box and holds periodic images of its own members (on
+    one hexahedron, all 24 members are images of the cell itself).  Stage
+    operator and two steps, inviscid and viscous, against the oracle."""
+    n = int(mesh[-1])
+    xyz, cells, per = (I.hex_cube if mesh.startswith("hex") else I.kuhn_cube)(n, jitter=0.0)
+    q = I.random_smooth_state(xyz, cells, seed=n, amp=0.05)
+
+    def close(a, b):
+        # relative to the operator, or to the state where the operator
+        # vanishes (one cell: the state is uniform and L is round-off)
+        scale = np.maximum(np.abs(b).max(axis=0), np.abs(q).max(axis=0))
+        return (np.abs(a - b).max(axis=0) / scale).max() < TOL
+
+    for kw in (dict(), dict(mu_ref=2e-3, Pr=0.72, tau_c=1.0)):
+        s, o = both(xyz, cells, per, q=q, **kw)
+        L, dL = s.stage_operator(0.01)
+        Lo, dLo = o.operator(0.01)
+        assert close(L, Lo) and close(dL, dLo)
+        s.step(2)
+        o.step(2)
+        qg, t, k = s.read()
+        qo, to, ko = o.get_state()
+        s.close()
+        assert k == ko == 2 and abs(t - to) <= 1e-14 * to
+        assert relerr(qg, qo) < TOL
