@@ -57,7 +57,7 @@ ROOF_TABLE = {
                                        src="profiles/flux_recon_op_counts.md (6 x 40^2 x 52 hex shell)"),
 }
 # DRAM bytes per cell of k_recon_rs as built, for the traffic of its roofline
-RECON_RS_DRAM = dict(bytes_per_cell=1893.4, sha="dc72fefb35ac", src="profiles/flux_recon_op_counts.md (48^3 x 6 tets)")
+RECON_RS_DRAM = dict(bytes_per_cell=1893.4, sha="2423f3ceece8", src="profiles/flux_recon_op_counts.md (48^3 x 6 tets)")
 # Algorithmic bytes per cell of one binary32 reconstruction launch (k_recon_rs)
 # on tetrahedra: binary64 pseudo-inverse rows (9K + 3 M KM) x 8 B, sub-stencil
 # positions M KM, stencil indices 4K, second moments and 1/h 7 x 8 B, the
