@@ -20,7 +20,11 @@ arrive over time.  The loop
     different solves overlaps on the device and newly admitted solves start
     while others are running,
   * reads a finished solve back, frees its memory and records its latency
-    (completion time minus arrival time).
+    (completion time minus arrival time),
+  * survives a device allocation that fails although the budget said it
+    would fit (HGKS_ENOMEM at creation): the reservation is given back, the
+    requests return to the queue in arrival order, and admission waits until
+    a running solve has freed its memory (``alloc_retries`` counts these).
 
 All numerics run in libhgks; this module only schedules.  Built host meshes
 are cached by geometry (the warm-cache case of a service that sees the same
@@ -144,6 +148,9 @@ class Server:
         used = 0
         self.peak_used = 0
         self.peak_active = 0
+        self.alloc_retries = 0
+        hold = False      # admission paused after a failed allocation, until a solve finishes
+        stalls = 0        # failed allocations in a row with nothing running
         worker = ThreadPoolExecutor(max_workers=1)
         t0 = time.perf_counter()
 
@@ -187,7 +194,13 @@ class Server:
                     pi += 1
                 busy = False
                 # admission in arrival order while memory allows
-                while queue:
+                if hold and not active and not creating:
+                    # nothing running will free memory: retry after a pause, a few times
+                    if stalls >= 3:
+                        raise MemoryError("device allocations keep failing with nothing running")
+                    time.sleep(0.05)
+                    hold = False
+                while queue and not hold:
                     head = queue[0]
                     mesh, q = self.cache.peek(head.kind, head.size)
                     if mesh.n_cells < self.small:
@@ -226,22 +239,45 @@ class Server:
                         used += need
                         creating.append((fut, [r for r, _, _ in group], need, 0, None))
                     else:
+                        added = 0
                         if gkey not in dev_bytes:
                             dev_bytes[gkey] = mesh.static_bytes
+                            added = mesh.static_bytes
                         inuse[gkey] = inuse.get(gkey, 0) + 1
                         work = mesh.work_bytes(self.precision)
                         used += need
                         fut = worker.submit(create_shared, gkey, mesh, q, head.params)
-                        creating.append((fut, [head], work, 0, gkey))
+                        creating.append((fut, [head], work, added, gkey))
                     self.peak_used = max(self.peak_used, used)
                     busy = True
                 # solvers that finished their set-up start stepping
                 for item in list(creating):
-                    fut, reqs, nb, _, gkey = item
+                    fut, reqs, nb, added, gkey = item
                     if not fut.done():
                         continue
                     creating.remove(item)
-                    solver = fut.result()  # a creation error ends the run
+                    try:
+                        solver = fut.result()  # any other creation error ends the run
+                    except H.HGKSError as e:
+                        if e.code != H.HGKS_ENOMEM:
+                            raise
+                        # the pool had less room than the budget assumed: give the
+                        # reservation back and queue the requests again
+                        used -= nb
+                        if gkey is not None:
+                            inuse[gkey] -= 1
+                            with dev_lock:
+                                made = gkey in dev
+                            if added and not made:  # the device mesh itself was not made
+                                used -= dev_bytes.pop(gkey)
+                        for r in reqs:
+                            r.admitted = math.nan
+                        queue = sorted(queue + list(reqs), key=lambda r: (r.arrival, r.rid))
+                        self.alloc_retries += 1
+                        stalls = stalls + 1 if not active and not creating else 0
+                        hold = True
+                        busy = True
+                        continue
                     if gkey is None:
                         real = solver.device_bytes
                         used += real - nb
@@ -273,6 +309,8 @@ class Server:
                             r.finished = tnow
                         sl.solver.close()
                         used -= sl.bytes
+                        hold = False
+                        stalls = 0
                         if sl.key is not None:
                             inuse[sl.key] -= 1
                         active.remove(sl)

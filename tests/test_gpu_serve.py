@@ -80,3 +80,25 @@ def test_solver_creation_is_ordered_while_the_gpu_is_busy():
         assert np.array_equal(got, q)
         small.close()
     big.sync()
+
+
+def test_a_failed_allocation_is_retried_and_results_stay_the_same():
+    """The library's allocation hook fails the third device allocation of the
+    run (a solver creation meets an exhausted pool although the budget said
+    it fits): the server gives the reservation back, queues the requests
+    again, admits them once memory is freed, and every result still equals
+    its result alone."""
+    cache = S.MeshCache()
+    reqs = mix()
+    cache.warm(reqs)
+    server = S.Server(mem_budget=8 << 30, chunk_steps=3, small_cells=1000, cache=cache)
+    H.test_fail_alloc(2)
+    try:
+        server.run(reqs, time_limit=300)
+    finally:
+        H.test_fail_alloc(-1)
+    assert server.alloc_retries == 1
+    for r in reqs:
+        q, t, n = alone(cache, r, server.flux_variant)
+        assert r.steps_done == n == 20 and r.t == t
+        assert np.array_equal(r.result, q), r.rid

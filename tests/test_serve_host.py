@@ -61,7 +61,15 @@ class _FakeCache:
         return self.meshes[key]
 
 
-def _fake_hgks(log):
+class _FakeError(RuntimeError):
+    def __init__(self, code):
+        super().__init__(f"fake failure {code}")
+        self.code = code
+
+
+def _fake_hgks(log, fail_at=()):
+    made = [0]
+
     class DeviceMesh:
         live = 0
 
@@ -76,6 +84,10 @@ def _fake_hgks(log):
 
     class Solver:
         def __init__(self, mesh, q, precision=None, **kw):
+            made[0] += 1
+            if made[0] in fail_at:  # this creation meets an exhausted pool
+                log.append(("enomem", made[0]))
+                raise _FakeError(-2)
             if isinstance(mesh, list):
                 self.member_cells = [m.n_cells for m in mesh]
                 log.append(("batch", tuple(self.member_cells)))
@@ -102,7 +114,8 @@ def _fake_hgks(log):
         def close(self):
             pass
 
-    return types.SimpleNamespace(DeviceMesh=DeviceMesh, Solver=Solver, HGKS_FP32_MIXED=1, HGKS_FP64=0)
+    return types.SimpleNamespace(DeviceMesh=DeviceMesh, Solver=Solver, HGKS_FP32_MIXED=1, HGKS_FP64=0,
+                                 HGKSError=_FakeError, HGKS_ENOMEM=-2)
 
 
 def _requests():
@@ -143,3 +156,32 @@ def test_server_logic_with_fake_solvers(monkeypatch):
     # the sphere 3 geometry is shared by its two requests unless evicted between them
     assert made.count(20000) <= 2
     assert all(getattr(r, "cells") in (500, 800, 20000, 30000, 40000) for r in reqs)
+
+
+def test_server_survives_failed_allocations(monkeypatch):
+    """A solver creation that fails with HGKS_ENOMEM although the budget said
+    it fits (the second and the fifth creation here): the requests go back to
+    the queue, admission waits for a running solve to finish, and every
+    request is still served once, with nothing leaked from the budget."""
+    log = []
+    monkeypatch.setattr(S, "H", _fake_hgks(log, fail_at=(2, 5)))
+    cache = _FakeCache(_cells)
+    budget = 110 * 40000 + 110 * 1600 + 65536 * 4
+    server = S.Server(mem_budget=budget, chunk_steps=7, small_cells=1000, max_batch=3, batch_cells=1500,
+                      cache=cache)
+    reqs = server.run(_requests(), time_limit=60)
+    assert server.alloc_retries == 2 and sum(1 for e in log if e[0] == "enomem") == 2
+    assert all(r.steps_done == 30 for r in reqs) and all(r.finished >= r.admitted >= 0 for r in reqs)
+    assert server.peak_used <= budget
+    assert S.H.DeviceMesh.live == 0
+
+
+def test_server_gives_up_when_allocations_keep_failing(monkeypatch):
+    """With nothing running to free memory, repeated failures end the run
+    with a MemoryError instead of spinning."""
+    import pytest
+
+    monkeypatch.setattr(S, "H", _fake_hgks([], fail_at=tuple(range(1, 100))))
+    server = S.Server(mem_budget=10 ** 12, chunk_steps=7, small_cells=1000, cache=_FakeCache(_cells))
+    with pytest.raises(MemoryError):
+        server.run(_requests()[:1], time_limit=60)
