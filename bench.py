@@ -38,8 +38,9 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# Executed operations per unit of the dominant kernels as built, from the ncu
-# operation counts summarised under profiles/ (file named in each entry), and
+# Executed operations per unit of the dominant kernels as built, from ncu
+# operation counts (the profile summary of the flux and reconstruction counts
+# under profiles/ gives the commands), and
 # DRAM bytes per unit where a capture measured them.  "sha" is the digest of
 # the kernel's sources (kernel_source_digest) that the counts were taken on:
 # when they have changed since, the line carries "counts_stale": true and no
@@ -48,16 +49,16 @@ sys.path.insert(0, ROOT)
 # fmul (mixed path), per launch divided by the units of the launch.
 ROOF_TABLE = {
     ("k_flux", "fp64", 3, False): dict(unit="face", flop=4786, dram=478.5, sha="79e699e45aa6",
-                                       src="profiles/flux_recon_op_counts.md (48^3 x 6 tets)"),
+                                       src="ncu operation counts and DRAM bytes on 48^3 x 6 tets"),
     ("k_flux", "fp64", 4, True): dict(unit="face", flop=13020, dram=541.4, sha="79e699e45aa6",
-                                      src="profiles/flux_recon_op_counts.md (6 x 40^2 x 52 hex shell)"),
+                                      src="ncu operation counts and DRAM bytes on the 6 x 40^2 x 52 hex shell"),
     ("k_flux", "mixed", 3, False): dict(unit="face", flop=4368, dram=247.6, sha="79e699e45aa6",
-                                        src="profiles/flux_recon_op_counts.md (48^3 x 6 tets)"),
+                                        src="ncu operation counts and DRAM bytes on 48^3 x 6 tets"),
     ("k_flux", "mixed", 4, True): dict(unit="face", flop=11739, dram=279.6, sha="79e699e45aa6",
-                                       src="profiles/flux_recon_op_counts.md (6 x 40^2 x 52 hex shell)"),
+                                       src="ncu operation counts and DRAM bytes on the 6 x 40^2 x 52 hex shell"),
 }
 # DRAM bytes per cell of k_recon_rs as built, for the traffic of its roofline
-RECON_RS_DRAM = dict(bytes_per_cell=1893.4, sha="2423f3ceece8", src="profiles/flux_recon_op_counts.md (48^3 x 6 tets)")
+RECON_RS_DRAM = dict(bytes_per_cell=1893.4, sha="2423f3ceece8", src="ncu operation counts and DRAM bytes on 48^3 x 6 tets")
 # Algorithmic bytes per cell of one binary32 reconstruction launch (k_recon_rs)
 # on tetrahedra: binary64 pseudo-inverse rows (9K + 3 M KM) x 8 B, sub-stencil
 # positions M KM, stencil indices 4K, second moments and 1/h 7 x 8 B, the
