@@ -57,15 +57,20 @@ ROOF_TABLE = {
     ("k_flux", "mixed", 4, True): dict(unit="face", flop=11739, dram=279.6, sha="79e699e45aa6",
                                        src="ncu operation counts and DRAM bytes on the 6 x 40^2 x 52 hex shell"),
 }
-# DRAM bytes per cell of k_recon_rs as built, for the traffic of its roofline
-RECON_RS_DRAM = dict(bytes_per_cell=1893.4, sha="2423f3ceece8", src="ncu operation counts and DRAM bytes on 48^3 x 6 tets")
-# Algorithmic bytes per cell of one binary32 reconstruction launch (k_recon_rs)
-# on tetrahedra: binary64 pseudo-inverse rows (9K + 3 M KM) x 8 B, sub-stencil
-# positions M KM, stencil indices 4K, second moments and 1/h 7 x 8 B, the
-# cell's own 32-byte state record, and the 50 binary32 coefficients written.
-# Neighbour records are gathered through L2 and not counted.
+# DRAM bytes per cell of k_recon_rs as built, keyed by stencil shape (K, M,
+# KM), for the traffic of its roofline
+RECON_RS_DRAM = {
+    (14, 4, 6): dict(bytes_per_cell=None, sha=None, src="ncu DRAM bytes on 48^3 x 6 tets"),
+    (24, 8, 3): dict(bytes_per_cell=None, sha=None, src="ncu DRAM bytes on the 6 x 40^2 x 52 hex shell"),
+}
+# Algorithmic bytes per cell of one binary32 reconstruction launch (k_recon_rs):
+# the cell's share of its block's binary32 record (pseudo-inverse rows
+# 9K + 3 M KM, second moments and 1/h 7, sub-stencil positions M KM / 4 rows of
+# 4 bytes per cell), stencil indices 4K, the cell's own 32-byte state record,
+# and the 50 binary32 coefficients written.  Neighbour records are gathered
+# through L2 and not counted.
 def recon_rs_bytes_per_cell(K: int, M: int = 4, KM: int = 6) -> int:
-    return (9 * K + 3 * M * KM) * 8 + M * KM + 4 * K + 7 * 8 + 32 + 50 * 4
+    return (9 * K + 7 + M * KM // 4 + 3 * M * KM) * 4 + 4 * K + 32 + 50 * 4
 
 
 FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12  # SMs x DFMA/clk x 2 flop x max SM clock
@@ -84,6 +89,25 @@ def kernel_source_digest(kernel: str = "k_flux") -> str:
         with open(os.path.join(ROOT, "paper_2407_00656_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
+
+
+def recon_roofline(K: int, M: int, KM: int, cells: int, ms_per_launch: float, with_ghosts: bool):
+    """roofline object of the binary32 reconstruction (k_recon_rs) from its
+    algorithmic bytes; with_ghosts: the time includes the ghost fill that
+    precedes each launch on meshes with boundaries (a lower bound on frac)."""
+    per_launch = recon_rs_bytes_per_cell(K, M, KM) * cells
+    ach = per_launch / (ms_per_launch * 1e-3) / 1e9
+    r = {"bound": "hbm", "kernel": f"k_recon_rs<{K}, {M}, {KM}> (binary32)", "achieved": ach,
+         "peak": HBM_PEAK_GBS, "unit": "GB/s", "frac": ach / HBM_PEAK_GBS, "bytes_per_launch": per_launch,
+         "bytes_per_cell": recon_rs_bytes_per_cell(K, M, KM), "ms_per_launch": ms_per_launch,
+         "peak_source": "MEASURED_PEAKS.json hbm_gbs", "traffic": None}
+    if with_ghosts:
+        r["time_includes"] = "the ghost fill before each launch"
+    e = RECON_RS_DRAM.get((K, M, KM))
+    if e and e["bytes_per_cell"] and e["sha"] == kernel_source_digest("k_recon_rs"):
+        r["traffic"] = e["bytes_per_cell"] * cells
+        r["traffic_source"] = e["src"]
+    return r
 
 
 def flux_roofline(precision: str, G: int, viscous: bool, faces: int, ms_per_launch: float):
@@ -352,16 +376,9 @@ def mixed_vs_fp64(H, w, stream, K, W, error_steps: int = 20):
            "kernel_ms_per_step": {"ghost+recon": prof[1], "flux": prof[2], "update": prof[3]},
            "error_vs_fp64": {"steps": error_steps, "l1_rel": l1, "linf_rel": linf, "dt": dts[0]},
            "roofline_flux": flux_roofline("mixed", G, viscous, nf, prof[2] / 2.0)}
-    if len(w["cells"][0]) == 4 and w["periods"] is not None:
-        per_launch = recon_rs_bytes_per_cell(kst) * nc
-        ach = per_launch / (prof[1] / 2 * 1e-3) / 1e9  # two reconstruction launches per step, no ghosts
-        res["roofline_recon"] = {"bound": "hbm", "kernel": "k_recon_rs (binary32)", "achieved": ach,
-                                 "peak": HBM_PEAK_GBS, "unit": "GB/s", "frac": ach / HBM_PEAK_GBS,
-                                 "bytes_per_launch": per_launch, "peak_source": "MEASURED_PEAKS.json hbm_gbs",
-                                 "traffic": None}
-        if RECON_RS_DRAM["sha"] == kernel_source_digest("k_recon_rs") and kst == 14:
-            res["roofline_recon"]["traffic"] = RECON_RS_DRAM["bytes_per_cell"] * nc
-            res["roofline_recon"]["traffic_source"] = RECON_RS_DRAM["src"]
+    if len(w["cells"][0]) == 4:
+        # two reconstruction launches per step
+        res["roofline_recon"] = recon_roofline(kst, 4, 6, nc, prof[1] / 2, w["periods"] is None)
     return res
 
 
@@ -406,6 +423,8 @@ def c3_run(H, K, W, error_steps):
                      "kernel_ms_per_step": {"finalize": prof[0], "ghost+recon": prof[1], "flux": prof[2],
                                             "update": prof[3]},
                      "roofline": flux_roofline(name, 4, True, nf, prof[2] / 2.0)}
+        if name == "mixed":
+            out[name]["roofline_recon"] = recon_roofline(base.stencil_size, 8, 3, nc, prof[1] / 2, True)
         # both precisions from the initial state with the FP64 path's first dt
         t = H.Solver(base.clone(), w["q"], precision=prec, **w["params"])
         if dt0 is None:

@@ -335,12 +335,13 @@ int make_dmesh(const hgks::HostMesh& m, std::vector<Member> members, const std::
   float* p_fdr32 = cv.take<float>((int64_t)m.G * 3 * m.nf);
   float* p_fn32 = cv.take<float>((int64_t)m.G * 3 * m.nf);
   float* p_fw32 = cv.take<float>((int64_t)m.G * m.nf);
+  float* p_rec32 = cv.take<float>(hgks::rec32_bytes(m.K, m.M, m.KM) / 4 * (m.ncp / 32));
   int32_t* p_cmesh = n > 1 ? cv.take<int32_t>(m.nc) : nullptr;
   if (cv.off > bytes) { g_err = "internal error: mesh arena too small"; return bail(HGKS_ENOMEM); }
   dm.volinv = p_volinv; dm.hdt = p_hdt; dm.hinv = p_hinv; dm.mom = p_mom; dm.sten = p_sten; dm.pinv0 = p_pinv0;
   dm.subidx = p_subidx; dm.pinvm = p_pinvm; dm.cface = p_cface; dm.gsrc = p_gsrc; dm.gtag = p_gtag; dm.gnrm = p_gnrm;
   dm.fown = p_fown; dm.fnbr = p_fnbr; dm.fdl = p_fdl; dm.fdr = p_fdr; dm.fn = p_fn; dm.fw = p_fw;
-  dm.fdl32 = p_fdl32; dm.fdr32 = p_fdr32; dm.fn32 = p_fn32; dm.fw32 = p_fw32;
+  dm.fdl32 = p_fdl32; dm.fdr32 = p_fdr32; dm.fn32 = p_fn32; dm.fw32 = p_fw32; dm.rec32 = p_rec32;
   dm.cmesh = p_cmesh;
   dm.perm = p_perm;
   std::vector<int32_t> perm32;
@@ -377,7 +378,7 @@ int make_dmesh(const hgks::HostMesh& m, std::vector<Member> members, const std::
   chk(up(p_fw, m.fw, st));
   if (p_cmesh) chk(up(p_cmesh, cmesh, st));
   if (ue == cudaSuccess) {
-    hgks::launch_face32(dm, st);
+    hgks::launch_round32(dm, st);
     ue = cudaGetLastError();
   }
   if (ue == cudaSuccess) ue = cudaStreamSynchronize(st);  // the host arrays may go away after return

@@ -174,9 +174,6 @@ __device__ __forceinline__ void recur(R* m, R U, R h2) {
 #ifndef HGKS_FAST_F32
 #define HGKS_FAST_F32 1
 #endif
-#ifndef HGKS_ERFC_AS
-#define HGKS_ERFC_AS 0
-#endif
 // Division, exponential and logarithm of the flux.  In binary32 they are the
 // hardware approximations (errors of a few units in the last place, far below
 // the mixed path's error against binary64; 9% off the viscous binary32 flux);
@@ -243,16 +240,6 @@ __device__ __forceinline__ void moments(const Prim<R>& p, int half, R Kint, Mom<
       // erfc(|s|) = ex erfcx(|s|) and erfc(-|s|) = 2 - erfc(|s|); measured
       // 3.5% faster than erfc on the FP64 flux (in binary32, erfc is faster)
       const R ec = ex * erfcx(fabs(s));
-      M.u[0] = R(0.5) * (s >= R(0) ? R(2) - ec : ec);
-    } else if constexpr (HGKS_ERFC_AS) {
-      // binary32: erfc(|s|) = t P(t) exp(-s^2), t = 1/(1 + 0.3275911 |s|),
-      // with P the degree-4 polynomial of Abramowitz and Stegun (1964),
-      // formula 7.1.26 (after Hastings), absolute error at most 1.5e-7, from
-      // the exponential already at hand; erfc(-|s|) = 2 - erfc(|s|)
-      const R t = fdiv(R(1), R(1) + R(0.3275911) * fabs(s));
-      const R poly = R(0.254829592) +
-                     t * (R(-0.284496736) + t * (R(1.421413741) + t * (R(-1.453152027) + t * R(1.061405429))));
-      const R ec = t * poly * ex;
       M.u[0] = R(0.5) * (s >= R(0) ? R(2) - ec : ec);
     } else {
       M.u[0] = R(0.5) * erfc(-s);

@@ -67,6 +67,14 @@ __global__ void __launch_bounds__(kRThreads, sizeof(Real) == 4 ? 2 : 1)
   const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
   const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t ntiles = (m.nc + kRC - 1) / kRC;
+  // mbarrier of the binary32 reconstruction's record copies and the parity
+  // of its next phase
+  __shared__ __align__(8) uint64_t rbar;
+  uint32_t rphase = 0;
+  if (F32) {
+    if (threadIdx.x == 0) mbar_init(&rbar, 1);
+    __syncthreads();
+  }
   for (int step = 0; step < nsteps; ++step) {
     if (blockIdx.x == 0)
       for (int i = threadIdx.x; i < m.nmesh; i += blockDim.x) finalize_one<true>(ctl + i, P.cfl);
@@ -81,8 +89,13 @@ __global__ void __launch_bounds__(kRThreads, sizeof(Real) == 4 ? 2 : 1)
       }
       if (!idle) {
         for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-          if constexpr (F32) recon_rs_block<K, M, KM, true>(m, P, w.Qf, coef, t * kRC, smem_raw);
-          else recon_block<Real, double, K, M, KM, false, true>(m, P, Qin, coef, ctl, t * kRC, smem_raw);
+          if constexpr (F32) {
+            // a record that never arrived ends the launch (the flag is set;
+            // the other blocks' barrier waits run out)
+            if (!recon_rs_block<K, M, KM, true>(m, P, w.Qf, coef, ctl, t * kRC, smem_raw, &rbar, rphase)) return;
+          } else {
+            recon_block<Real, double, K, M, KM, false, true>(m, P, Qin, coef, ctl, t * kRC, smem_raw);
+          }
           __syncthreads();  // the next tile reuses the shared memory
         }
       }

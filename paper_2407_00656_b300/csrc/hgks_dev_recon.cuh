@@ -1,6 +1,6 @@
 // hgks_dev_recon.cuh -- third-order WENO reconstruction kernels (Section
 // 2.3, Eqs. polys and weno): k_recon (bulk-copy staged or direct) and
-// k_recon_rs (binary32, staged through registers).
+// k_recon_rs (binary32, from per-block records moved by bulk copies).
 #pragma once
 
 #include "hgks_dev_common.cuh"
@@ -303,54 +303,45 @@ __global__ void __launch_bounds__(kRThreads) k_recon(DevMesh m, DevParams P, con
 }
 
 // WENO reconstruction in binary32 (mixed precision), one block per kRC = 32
-// cells with one warp per conservative variable, as k_recon, but with every
-// input of the block staged in shared memory by all 160 threads before any
-// arithmetic:
-//   - the stencil neighbours' states, one 32-byte record (all five
-//     variables) per neighbour;
-//   - the block's rows of the binary64 pseudo-inverses, rounded to binary32
-//     on the way in (cvt<float>, the rounding k_recon applies), so the tile
-//     takes half the shared memory of a binary64 tile and more blocks fit on
-//     an SM;
-//   - the sub-stencil positions, the cells' own states, second moments and
-//     1/h.
-// The copy loops issue their loads back to back (coalesced rows of 32 cells
-// for the per-cell arrays), so each thread keeps many loads in flight.  The
-// arithmetic and its order are those of k_recon.
-// Two ways to take less shared memory, used where they let more blocks share
-// an SM (the choice is made at compile time from the sizes):
-//   - "phased": the tile holds the quadratic rows (9K) first; once every
-//     warp has formed its quadratic coefficients, the linear sub-stencil rows
-//     replace them, so the tile needs max(9K, 3 M KM) rows, not the sum;
-//   - "lean": the own-state and geometry rows are left out, and each thread
-//     loads its cell's state, second moments and 1/h into registers.
-// The block count is capped by the registers a thread needs (about 56 on
-// tetrahedra, 66 on hexahedra, 86 at stencil size 26, measured with ptxas),
-// and the kernel's launch bounds ask the compiler for that count.
+// cells with one warp per conservative variable, as k_recon.  The block's
+// binary32 reconstruction record (pseudo-inverse rows, second moments, 1/h
+// and sub-stencil positions, rounded once when the mesh was made, as
+// cvt<float> rounds them: see rec32_bytes) is contiguous in memory, so warp 0
+// moves it into shared memory with a few bulk asynchronous copies completed
+// on an mbarrier, while every thread gathers stencil neighbours' states (one
+// 32-byte record of all five variables per neighbour) into shared memory and
+// its own cell's state into a register.  The arithmetic and its order are
+// those of k_recon.
+// "Phased": where it lets more blocks share an SM, the first copy stops
+// before the linear sub-stencil rows; once every warp has formed its
+// quadratic coefficients, a second copy puts the linear rows over the
+// quadratic ones, so the tile needs 9K (not 9K + 3 M KM) inverse rows.
+// Blocks per SM: as many as shared memory and registers (about 56 per thread
+// on tetrahedra, 66 on hexahedra, 86 at stencil size 26, measured with ptxas)
+// allow; the kernel's launch bounds ask the compiler for that count.
 template <int K, int M, int KM>
 struct ReconSmemF {
+  static_assert(M * KM % 4 == 0 && 3 * M * KM <= 9 * K, "record layout");
   static constexpr int R0 = 9 * K, R1 = M * 3 * KM;  // quadratic and linear rows
-  static constexpr size_t nbr = sizeof(float) * 5 * K * kRC;  // neighbour states [5][K][kRC]
-  static constexpr size_t own = sizeof(float) * 5 * kRC;      // own states [5][kRC]
-  static constexpr size_t geo = sizeof(float) * 7 * kRC;      // mom (6) and 1/h [7][kRC]
-  static constexpr size_t sub = (size_t)M * KM * kRC;         // sub-stencil positions
-  static constexpr size_t rows_f = sizeof(float) * (R0 + R1) * kRC, rows_p = sizeof(float) * (R0 > R1 ? R0 : R1) * kRC;
+  static constexpr int RG = R0;                       // row of the first second moment
+  static constexpr int RP = R0 + 7;                   // first row of sub-stencil positions
+  static constexpr int RL = RP + M * KM / 4;          // first linear row in the record
+  static constexpr size_t rec = (size_t)rec32_bytes(K, M, KM);  // the block's record
+  static constexpr size_t head = (size_t)RL * 128;               // the record up to the linear rows
+  static constexpr size_t nbr = sizeof(float) * 5 * K * kRC;     // neighbour states [5][K][kRC]
   // blocks per SM: 228 KB of shared memory, 1 KB reserved per block; registers
   static constexpr int fit(size_t b) { return (int)(233472 / (b + 1024)); }
   static constexpr int reg_cap = 65536 / (kRThreads * (M == 4 ? 56 : (K <= 24 ? 66 : 86)));
   static constexpr int cap(int b) { return b < reg_cap ? b : reg_cap; }
-  static constexpr int b_full = cap(fit(rows_f + nbr + own + geo + sub)), b_lean = cap(fit(rows_f + nbr + sub)),
-                       b_ph = cap(fit(rows_p + nbr + own + geo + sub)), b_phl = cap(fit(rows_p + nbr + sub));
-  static constexpr int best = b_full > b_lean ? (b_full > b_ph ? (b_full > b_phl ? b_full : b_phl)
-                                                               : (b_ph > b_phl ? b_ph : b_phl))
-                                              : (b_lean > b_ph ? (b_lean > b_phl ? b_lean : b_phl)
-                                                               : (b_ph > b_phl ? b_ph : b_phl));
-  // the simplest layout that reaches the best count
-  static constexpr bool phased = b_full < best && b_lean < best;
-  static constexpr bool lean = phased ? b_ph < best : b_full < best;
-  static constexpr size_t tile = phased ? rows_p : rows_f;  // binary32 rows
-  static constexpr size_t bytes = tile + nbr + (lean ? 0 : own + geo) + sub;
-  static constexpr int blocks = best;
+  static constexpr bool phased = cap(fit(head + nbr)) > cap(fit(rec + nbr));
+  static constexpr size_t tile = phased ? head : rec;
+  static constexpr size_t bytes = tile + nbr;
+  static constexpr int blocks = cap(fit(bytes));
+  static constexpr int LB = phased ? 0 : RL;  // tile row of the first linear row
+  // copies in pieces of at most 4 KB, one per lane of warp 0
+  static constexpr int piece = 4096;
+  static_assert(rec % 16 == 0 && (rec + piece - 1) / piece <= 32, "bulk copies of the record");
+  static_assert(tile >= sizeof(float) * kRC * (kCoefRec32 + 1), "the output staging fits in the tile");
 };
 
 // The least-squares polynomials of one (variable, cell) thread from a
@@ -429,160 +420,105 @@ __device__ __forceinline__ void rs_linear(const float* tile, const float* snbr, 
   }
 }
 
+// Bytes [off, off + len) of a block's record (rec) to shared memory at dst,
+// completing on bar; called by warp 0.
+__device__ __forceinline__ void rec_copy(unsigned char* dst, const char* rec, size_t off, size_t len, uint64_t* bar) {
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) {
+    // shared memory read and written by the generic proxy before (earlier
+    // phase, earlier tile of a persistent launch) is overwritten by the copies
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(bar, (uint32_t)len);
+  }
+  __syncwarp();
+  const size_t o = (size_t)lane * 4096;
+  if (o < len) bulk_g2s(dst + o, rec + off + o, (uint32_t)(len - o < 4096 ? len - o : 4096), bar);
+}
+
+// One block of k_recon_rs at cells c0 .. c0 + 31.  bar: the block's
+// mbarrier (initialised, count 1); phase: the parity of bar's next phase,
+// advanced by each copy this call waits for.  Returns false, with
+// FLAG_TIMEOUT set, if a copy did not land within the bounded wait.
 template <int K, int M, int KM, bool COH = false>
-__device__ __forceinline__ void recon_rs_block(const DevMesh& m, const DevParams& P, const float* __restrict__ Qf,
-                                               float* __restrict__ coef, int64_t c0, unsigned char* smem_raw) {
+__device__ __forceinline__ bool recon_rs_block(const DevMesh& m, const DevParams& P, const float* __restrict__ Qf,
+                                               float* __restrict__ coef, Control* __restrict__ ctl, int64_t c0,
+                                               unsigned char* smem_raw, uint64_t* bar, uint32_t& phase) {
   using S = ReconSmemF<K, M, KM>;
-  float* tile = reinterpret_cast<float*>(smem_raw);                              // [kRows][kRC]
-  float* snbr = reinterpret_cast<float*>(smem_raw + S::tile);                    // [5][K][kRC]
-  float* sown = reinterpret_cast<float*>(smem_raw + S::tile + S::nbr);           // [5][kRC] (not lean)
-  float* sgeo = reinterpret_cast<float*>(smem_raw + S::tile + S::nbr + S::own);  // [7][kRC] (not lean)
-  uint8_t* ssub = smem_raw + S::tile + S::nbr + (S::lean ? 0 : S::own + S::geo);  // [M*KM][kRC]
-  const int64_t nc = m.nc, ncp = m.ncp;
-  const int t = threadIdx.x;
+  float* tile = reinterpret_cast<float*>(smem_raw);                  // [rows][kRC]
+  const uint8_t* ssub = smem_raw + (size_t)S::RP * 128;              // [M*KM][kRC]
+  float* snbr = reinterpret_cast<float*>(smem_raw + S::tile);        // [5][K][kRC]
+  const char* rec = reinterpret_cast<const char*>(m.rec32) + (size_t)(c0 / kRC) * S::rec;
+  const int64_t nc = m.nc;
+  const int t = threadIdx.x, lane = t & 31, v = t >> 5;
   const int nv = nc - c0 < kRC ? (int)(nc - c0) : kRC;  // cells of this block
-  // With 5 warps of 32 lanes, thread (v, lane) stages column `lane` of the
-  // rows v, v + 5, v + 10, ... of every per-cell array, so its addresses
-  // advance by a fixed stride.
-  const int lane = t & 31, v = t >> 5;
   const bool live = lane < nv;
-  // 1. stencil indices of this thread's neighbour entries (entry K: the cell
-  // itself, staged unless lean)
-  constexpr int KE = S::lean ? K : K + 1;
-  constexpr int NE = (KE + 4) / 5;
+  // a bounded wait for the copies of the current phase; false: flag, one
+  // more bounded wait for the copies in flight, and leave (only a stalled
+  // memory system explains a block's own copies, under 40 KB, not landing
+  // within about a second; the host reports HGKS_ETIMEOUT)
+  auto landed = [&]() {
+    const bool ok = __syncthreads_and(mbar_wait_bounded(bar, phase));
+    if (!ok) {
+      if (t == 0) atomicOr(&ctl->flags, FLAG_TIMEOUT);
+      mbar_wait_bounded(bar, phase);
+    }
+    phase ^= 1u;
+    return ok;
+  };
+  // 1. the block's record (the head only, phased)
+  if (v == 0) rec_copy(smem_raw, rec, 0, S::tile, bar);
+  // 2. stencil neighbours' states and the cell's own (overlap the copies).
+  // Thread (v, lane) fetches entries k = v, v + 5, ... of column `lane`.
+  constexpr int NE = (K + 4) / 5;
   int32_t jn[NE];
 #pragma unroll
   for (int i = 0; i < NE; ++i) {
     const int k = v + 5 * i;
-    jn[i] = (k < K && live) ? __ldcs(m.sten + (int64_t)k * nc + c0 + lane) : (int32_t)(c0 + lane);
+    jn[i] = (k < K && live) ? __ldcs(m.sten + (int64_t)k * nc + c0 + lane) : 0;
   }
-  // 2. first batch of pseudo-inverse rows (binary64, read once: streaming
-  // loads).  Thread (v, lane) copies rows v + 5 j: J0 rows of pinv0 for
-  // every v, then one more row for v < T0 (likewise J1, T1 for pinvm); the
-  // row counts are compile-time constants, so only the tail row is guarded.
-  constexpr int R0 = 9 * K, R1 = M * 3 * KM;  // rows of pinv0 and pinvm
-  constexpr int J0 = R0 / 5, T0 = R0 - 5 * J0, J1 = R1 / 5, T1 = R1 - 5 * J1;
-  // rows per batch of loads, measured: 12 in the tile layouts (8 is 5%
-  // slower on tetrahedra, 16 slower on hexahedra); 8 in the lean layout,
-  // whose register-held own state and geometry leave less room (12 took the
-  // K = 26 hybrid shell from 2.52 to 4.58 ms per step)
-  constexpr int B = S::lean ? 8 : 12;
-  static_assert(J0 >= B, "the first batch is a full one");
-  constexpr int RS = 5 * kRC;  // shared-memory stride between a thread's rows
-  const int64_t step = 5 * ncp;
-  const double* p0 = m.pinv0 + (int64_t)v * ncp + c0 + lane;
-  float* d0 = tile + v * kRC + lane;
-  double pv[B];
-#pragma unroll
-  for (int i = 0; i < B; ++i) pv[i] = __ldcs(p0 + i * step);
-  // 3. neighbour and own state records (32 bytes each)
+  const float qv = live ? ldro<COH>(Qf + 8 * (c0 + lane) + v) : 0.f;
   float4 qa[NE];
   float qb[NE];
-  float qown = 0.f, gl[7];
-  if constexpr (S::lean) {
-    if (live) {
-      qown = ldro<COH>(Qf + 8 * (c0 + lane) + v);
-#pragma unroll
-      for (int r = 0; r < 7; ++r) gl[r] = cvt<float>(r < 6 ? m.mom[(int64_t)r * nc + c0 + lane] : m.hinv[c0 + lane]);
-    }
-  }
 #pragma unroll
   for (int i = 0; i < NE; ++i) {
-    if (v + 5 * i < KE && live) {
+    if (v + 5 * i < K && live) {
       qa[i] = ldro<COH>(reinterpret_cast<const float4*>(Qf + 8 * (int64_t)jn[i]));
       qb[i] = ldro<COH>(Qf + 8 * (int64_t)jn[i] + 4);
     }
   }
-  // 4. the first batch to binary32, then the remaining rows in batches
-#pragma unroll
-  for (int i = 0; i < B; ++i) d0[i * RS] = cvt<float>(pv[i]);
-  {
-    const double* q = p0 + B * step;
-    float* d = d0 + B * RS;
-#pragma unroll 1
-    for (int j = B; j + B <= J0; j += B) {
-#pragma unroll
-      for (int i = 0; i < B; ++i) pv[i] = __ldcs(q + i * step);
-#pragma unroll
-      for (int i = 0; i < B; ++i) d[i * RS] = cvt<float>(pv[i]);
-      q += B * step;
-      d += B * RS;
-    }
-    constexpr int REM0 = (J0 - B) % B;
-#pragma unroll
-    for (int i = 0; i < REM0; ++i) pv[i] = __ldcs(q + i * step);
-#pragma unroll
-    for (int i = 0; i < REM0; ++i) d[i * RS] = cvt<float>(pv[i]);
-    if (v < T0) tile[(5 * J0 + v) * kRC + lane] = cvt<float>(__ldcs(p0 + J0 * step));
-  }
-  // linear sub-stencil rows, at tile row R0 (after the quadratic rows) or,
-  // phased, at row 0 once the quadratic coefficients are formed
-  auto stage_linear = [&](float* dbase) {
-    const double* p1 = m.pinvm + (int64_t)v * ncp + c0 + lane;
-    const double* q = p1;
-    float* d = dbase;
-#pragma unroll 1
-    for (int j = 0; j + B <= J1; j += B) {
-#pragma unroll
-      for (int i = 0; i < B; ++i) pv[i] = __ldcs(q + i * step);
-#pragma unroll
-      for (int i = 0; i < B; ++i) d[i * RS] = cvt<float>(pv[i]);
-      q += B * step;
-      d += B * RS;
-    }
-    constexpr int REM1 = J1 % B;
-#pragma unroll
-    for (int i = 0; i < REM1; ++i) pv[i] = __ldcs(q + i * step);
-#pragma unroll
-    for (int i = 0; i < REM1; ++i) d[i * RS] = cvt<float>(pv[i]);
-    if (v < T1) dbase[J1 * RS] = cvt<float>(__ldcs(p1 + J1 * step));
-  };
-  if constexpr (!S::phased) stage_linear(d0 + R0 * kRC);
-  // 5. neighbour states to shared memory ([5][K][kRC]; own states [5][kRC])
 #pragma unroll
   for (int i = 0; i < NE; ++i) {
     const int k = v + 5 * i;
-    if (k < KE && live) {
-      float* dst = k < K ? snbr + k * kRC + lane : sown + lane;
-      const int vs = k < K ? K * kRC : kRC;
+    if (k < K && live) {
+      float* dst = snbr + k * kRC + lane;
       dst[0] = qa[i].x;
-      dst[vs] = qa[i].y;
-      dst[2 * vs] = qa[i].z;
-      dst[3 * vs] = qa[i].w;
-      dst[4 * vs] = qb[i];
+      dst[K * kRC] = qa[i].y;
+      dst[2 * K * kRC] = qa[i].z;
+      dst[3 * K * kRC] = qa[i].w;
+      dst[4 * K * kRC] = qb[i];
     }
   }
-  // 6. sub-stencil positions, second moments and 1/h
-  for (int r = v; r < M * KM; r += 5) ssub[r * kRC + lane] = m.subidx[(int64_t)r * ncp + c0 + lane];
-  if constexpr (!S::lean)
-    for (int r = v; r < 7; r += 5)
-      if (live) sgeo[r * kRC + lane] = cvt<float>(r < 6 ? m.mom[(int64_t)r * nc + c0 + lane] : m.hinv[c0 + lane]);
-  __syncthreads();
-  float res[10];
-  // least-squares polynomials (rs_quadratic, rs_linear)
-  constexpr int LB = S::phased ? 0 : R0;  // tile row of the first linear row
-  float a[9];
-  float b[M][3];
-  float qv = 0.f;
-  if (live) {
-    qv = S::lean ? qown : sown[v * kRC + lane];
-    rs_quadratic<K, M>(tile, snbr, qv, v, lane, a);
-  }
+  // 3. the copies have landed and the neighbour states are in place
+  if (!landed()) return false;
+  float a[9], b[M][3];
+  if (live) rs_quadratic<K, M>(tile, snbr, qv, v, lane, a);
   if constexpr (S::phased) {
     __syncthreads();  // every warp has read its quadratic rows
-    stage_linear(d0);
-    __syncthreads();
+    if (v == 0) rec_copy(smem_raw, rec, S::head, S::rec - S::head, bar);
+    if (!landed()) return false;
   }
+  float res[10];
   if (live) {
-    rs_linear<K, M, KM, LB>(tile, snbr, ssub, qv, v, lane, b);
+    rs_linear<K, M, KM, S::LB>(tile, snbr, ssub, qv, v, lane, b);
     float mi[6];
 #pragma unroll
-    for (int q = 0; q < 6; ++q) mi[q] = S::lean ? gl[q] : sgeo[q * kRC + lane];
-    const float hi = S::lean ? gl[6] : sgeo[6 * kRC + lane];
+    for (int q = 0; q < 6; ++q) mi[q] = tile[(S::RG + q) * kRC + lane];
+    const float hi = tile[(S::RG + 6) * kRC + lane];
     const float glin = P.f_glin, g0 = 1.f - float(M) * glin, eps = P.f_eps;
     recon_finish<float, M>(a, b, qv, mi, hi, glin, g0, eps, res);
   }
   write_block_records<float>(tile, res, live, lane, v, nv, coef, c0);
+  return true;
 }
 
 template <int K, int M, int KM>
@@ -590,8 +526,12 @@ __global__ void __launch_bounds__(kRThreads, ReconSmemF<K, M, KM>::blocks) k_rec
                                                                                  const float* __restrict__ Qf,
                                                         float* __restrict__ coef, Control* __restrict__ ctl) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
   if (m.nmesh == 1 && ctl->dt == 0.0) return;  // uniform over the grid (a batch computes every member)
-  recon_rs_block<K, M, KM>(m, P, Qf, coef, (int64_t)blockIdx.x * kRC, smem_raw);
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  uint32_t phase = 0;
+  recon_rs_block<K, M, KM>(m, P, Qf, coef, ctl, (int64_t)blockIdx.x * kRC, smem_raw, &bar, phase);
 }
 
 }  // namespace

@@ -119,6 +119,37 @@ __global__ void k_round32(const double* __restrict__ a, float* __restrict__ b, i
   if (i < n) b[i] = cvt<float>(a[i]);
 }
 
+// Binary32 reconstruction records (layout: rec32_bytes), one thread per
+// 4-byte word of a record.
+__global__ void k_rec32(DevMesh m, float* __restrict__ rec) {
+  const int R0 = 9 * m.K;
+  const int64_t words = rec32_bytes(m.K, m.M, m.KM) / 4;
+  const int64_t qend = (int64_t)(R0 + 7) * 32;           // quadratic and geometry rows
+  const int64_t pend = qend + (int64_t)m.M * m.KM * 8;  // and the position bytes
+  const int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (i >= words * (m.ncp / 32)) return;
+  const int64_t b = i / words, w = i - b * words;
+  if (w < pend && w >= qend) {
+    // bytes 4e .. 4e+3 of the position rows ([M KM][32])
+    const int64_t e = w - qend;
+    uint32_t word = 0;
+    for (int k = 0; k < 4; ++k) {
+      const int64_t y = 4 * e + k, r = y / 32, c = b * 32 + (y - r * 32);
+      word |= (uint32_t)m.subidx[r * m.ncp + c] << (8 * k);
+    }
+    reinterpret_cast<uint32_t*>(rec)[i] = word;
+    return;
+  }
+  const int64_t e = w < qend ? w : w - pend;
+  const int r = (int)(e / 32);
+  const int64_t c = b * 32 + (e - (int64_t)r * 32);
+  double x = 0.0;
+  if (w >= pend) x = m.pinvm[(int64_t)r * m.ncp + c];
+  else if (r < R0) x = m.pinv0[(int64_t)r * m.ncp + c];
+  else if (c < m.nc) x = r < R0 + 6 ? m.mom[(int64_t)(r - R0) * m.nc + c] : m.hinv[c];
+  rec[i] = cvt<float>(x);
+}
+
 // Binary32 copy of the state (mixed precision).
 // Caller order and layout ([n][5], member-local index perm[c]) to the internal
 // structure-of-arrays order of cells coff .. coff+n-1, and back.

@@ -44,7 +44,25 @@ struct DevMesh {
   const float* fdr32;     // [3G][nf]
   const float* fn32;      // [3G][nf]
   const float* fw32;      // [G][nf]
+  // binary32 reconstruction records, one per block of 32 consecutive cells
+  // (layout: rec32_bytes), read by the binary32 reconstruction
+  const float* rec32;     // [ncp/32][rec32_bytes(K, M, KM) / 4]
 };
+
+// Binary32 reconstruction record of a block of 32 consecutive cells: the
+// binary32 roundings (cvt<float>) of the block's inputs to the
+// reconstruction, contiguous so that bulk copies move them.  Rows of 32
+// 4-byte values, one per cell of the block (zero past the last cell): the
+// 9K rows of pinv0, the six second moments, 1/h, the M KM rows of
+// sub-stencil positions (one byte per cell, so M KM / 4 rows), then the
+// 3 M KM rows of pinvm.  A record's size is a multiple of 128 bytes.
+#ifdef __CUDACC__
+#define HGKS_HD __host__ __device__
+#else
+#define HGKS_HD
+#endif
+HGKS_HD constexpr int rec32_rows(int K, int M, int KM) { return 9 * K + 7 + M * KM / 4 + 3 * M * KM; }
+HGKS_HD constexpr int64_t rec32_bytes(int K, int M, int KM) { return (int64_t)rec32_rows(K, M, KM) * 128; }
 
 // Physical and numerical parameters as the kernels use them.
 struct DevParams {
@@ -187,9 +205,10 @@ void launch_reset(const DevMesh& m, const DevParams& p, const DevWork& w, int pr
 // of Q ([5][nce]).  `in` and `out` are device buffers.
 void launch_state_in(const DevMesh& m, const double* in, int64_t coff, int64_t n, double* Q, cudaStream_t s);
 void launch_state_out(const DevMesh& m, const double* Q, int64_t coff, int64_t n, double* out, cudaStream_t s);
-// Fill the binary32 face geometry (fdl32, fdr32, fn32, fw32) of a device
-// mesh from its binary64 arrays.
-void launch_face32(const DevMesh& m, cudaStream_t s);
+// Fill the binary32 tables of a device mesh from its binary64 arrays: the
+// face geometry (fdl32, fdr32, fn32, fw32) and the reconstruction records
+// (rec32).
+void launch_round32(const DevMesh& m, cudaStream_t s);
 // L and dL/dt of the current state for step dt into Qs[0:5] and R (as L) -- test path.
 void launch_operator(const DevMesh& m, const DevParams& p, const DevWork& w, int precision, double dt,
                      double* L, double* dL, cudaStream_t s);

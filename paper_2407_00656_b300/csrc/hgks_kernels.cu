@@ -52,13 +52,16 @@ void stage_pair(const DevMesh& m, const DevParams& p, const DevWork& w, bool mix
 
 }  // namespace
 
-void launch_face32(const DevMesh& m, cudaStream_t s) {
+void launch_round32(const DevMesh& m, cudaStream_t s) {
   const int64_t n3 = (int64_t)3 * m.G * m.nf, n1 = (int64_t)m.G * m.nf;
-  if (n3 == 0) return;
-  k_round32<<<blocks(n3), kBlock, 0, s>>>(m.fdl, const_cast<float*>(m.fdl32), n3);
-  k_round32<<<blocks(n3), kBlock, 0, s>>>(m.fdr, const_cast<float*>(m.fdr32), n3);
-  k_round32<<<blocks(n3), kBlock, 0, s>>>(m.fn, const_cast<float*>(m.fn32), n3);
-  k_round32<<<blocks(n1), kBlock, 0, s>>>(m.fw, const_cast<float*>(m.fw32), n1);
+  if (n3 > 0) {
+    k_round32<<<blocks(n3), kBlock, 0, s>>>(m.fdl, const_cast<float*>(m.fdl32), n3);
+    k_round32<<<blocks(n3), kBlock, 0, s>>>(m.fdr, const_cast<float*>(m.fdr32), n3);
+    k_round32<<<blocks(n3), kBlock, 0, s>>>(m.fn, const_cast<float*>(m.fn32), n3);
+    k_round32<<<blocks(n1), kBlock, 0, s>>>(m.fw, const_cast<float*>(m.fw32), n1);
+  }
+  const int64_t nr = rec32_bytes(m.K, m.M, m.KM) / 4 * (m.ncp / 32);
+  if (nr > 0) k_rec32<<<blocks(nr), kBlock, 0, s>>>(m, const_cast<float*>(m.rec32));
 }
 
 void launch_setdt(const DevMesh& m, const DevWork& w, double dt, cudaStream_t s) {

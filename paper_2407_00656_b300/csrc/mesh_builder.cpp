@@ -825,6 +825,7 @@ int64_t mesh_static_bytes(const HostMesh& m, int nmesh) {
   b += al(4 * nf) * 2;                         // fown, fnbr
   b += al(8 * (int64_t)m.G * 3 * nf) * 3 + al(8 * (int64_t)m.G * nf);  // fdl fdr fn fw
   b += al(4 * (int64_t)m.G * 3 * nf) * 3 + al(4 * (int64_t)m.G * nf);  // their binary32 roundings
+  b += al(rec32_bytes(m.K, m.M, m.KM) * (ncp / 32));  // binary32 reconstruction records
   if (nmesh > 1) b += al(4 * nc);              // member of each cell
   return b + 256;
 }
