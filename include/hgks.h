@@ -95,7 +95,9 @@ typedef struct {
  *                  (gamma_0 = 1 - M weno_gamma_lin), Section 2.3.
  *   q_inf          conservative far-field free stream.
  *   precision      HGKS_FP64, or HGKS_FP32_MIXED: reconstruction and flux
- *                  in binary32, geometry, inverses and S2O4 in binary64.
+ *                  in binary32, geometry, inverses and S2O4 in binary64
+ *                  (the binary32 kernels read binary32 roundings of the
+ *                  geometry and inverses, made once per device mesh).
  *   use_graph      1: replay each step as one captured CUDA graph.
  *   autotune       1: at hgks_init, time the kernel variants (flux with one
  *                  thread per face or one per Gauss point; reconstruction
@@ -114,8 +116,9 @@ typedef struct {
  *                  graph launches, for small meshes and batches of them;
  *                  measured slower than graph launches on B300, so off by
  *                  default.  The flux runs per face and the reconstruction
- *                  variants are fixed (binary32: register-staged; binary64:
- *                  rows read directly), whatever hgks_set_tuning selected.
+ *                  variants are fixed (binary32: per-block records;
+ *                  binary64: rows read directly), whatever hgks_set_tuning
+ *                  selected.
  *                  Results agree with the separate kernels to a few units in
  *                  the last place.  A grid barrier that waits more than
  *                  about a second ends the launch with HGKS_ETIMEOUT at the
