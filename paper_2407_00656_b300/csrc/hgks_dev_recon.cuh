@@ -135,28 +135,28 @@ constexpr int kRC = 32;
 constexpr int kRThreads = 5 * kRC;
 
 // Coefficient records of the block's cells (consecutive, so their records
-// are one contiguous run of memory): each (variable, cell) thread puts its
-// 10 reals into shared memory (pitch record + 1, which spreads a warp's
-// stores over the banks), then the block writes the run with coalesced
+// are one contiguous run of memory): each (variable, cell) result is put
+// into shared memory (pitch record + 1, which spreads a warp's stores over
+// the banks), then the block's NT threads write the run with coalesced
 // stores.  smem must hold kRC x (record + 1) reals and no longer be read by
-// any warp's arithmetic; every thread of the block calls this.
+// any warp's arithmetic; every thread of the block calls these.
 template <typename Real>
-__device__ __forceinline__ void write_block_records(Real* smem, const Real res[10], bool live, int lane, int v,
-                                                    int nv, Real* __restrict__ coef, int64_t c0) {
+__device__ __forceinline__ void stage_record(Real* smem, const Real res[10], int lane, int v) {
   constexpr int REC = coef_rec<Real>(), PITCH = REC + 1;
-  __syncthreads();
-  if (live) {
 #pragma unroll
-    for (int j = 0; j < 10; ++j) smem[lane * PITCH + v * 10 + j] = res[j];
-    if (v == 0)
-      for (int j = 50; j < REC; ++j) smem[lane * PITCH + j] = Real(0);
-  }
+  for (int j = 0; j < 10; ++j) smem[lane * PITCH + v * 10 + j] = res[j];
+  if (v == 0)
+    for (int j = 50; j < REC; ++j) smem[lane * PITCH + j] = Real(0);
+}
+template <typename Real, int NT>
+__device__ __forceinline__ void flush_records(const Real* smem, int nv, Real* __restrict__ coef, int64_t c0) {
+  constexpr int REC = coef_rec<Real>(), PITCH = REC + 1;
   __syncthreads();
   Real* dst = coef + c0 * REC;
   // element e = l REC + r of the run; (l, r) advance by a constant step
-  constexpr int DL = kRThreads / REC, DR = kRThreads % REC;
+  constexpr int DL = NT / REC, DR = NT % REC;
   int l = threadIdx.x / REC, r = threadIdx.x - (threadIdx.x / REC) * REC;
-  for (int e = threadIdx.x; e < nv * REC; e += kRThreads) {
+  for (int e = threadIdx.x; e < nv * REC; e += NT) {
     dst[e] = smem[l * PITCH + r];
     l += DL;
     r += DR;
@@ -165,6 +165,13 @@ __device__ __forceinline__ void write_block_records(Real* smem, const Real res[1
       ++l;
     }
   }
+}
+template <typename Real>
+__device__ __forceinline__ void write_block_records(Real* smem, const Real res[10], bool live, int lane, int v,
+                                                    int nv, Real* __restrict__ coef, int64_t c0) {
+  __syncthreads();
+  if (live) stage_record<Real>(smem, res, lane, v);
+  flush_records<Real, kRThreads>(smem, nv, coef, c0);
 }
 
 // WENO reconstruction, one block per kRC = 32 consecutive cells with one warp
@@ -303,7 +310,9 @@ __global__ void __launch_bounds__(kRThreads) k_recon(DevMesh m, DevParams P, con
 }
 
 // WENO reconstruction in binary32 (mixed precision), one block per kRC = 32
-// cells with one warp per conservative variable, as k_recon.  The block's
+// cells with one warp per conservative variable, as k_recon, or ("paired")
+// three warps, two of which serve two variables each, so that every row a
+// thread reads from shared memory feeds two variables.  The block's
 // binary32 reconstruction record (pseudo-inverse rows, second moments, 1/h
 // and sub-stencil positions, rounded once when the mesh was made, as
 // cvt<float> rounds them: see rec32_bytes) is contiguous in memory, so warp 0
@@ -317,11 +326,15 @@ __global__ void __launch_bounds__(kRThreads) k_recon(DevMesh m, DevParams P, con
 // quadratic coefficients, a second copy puts the linear rows over the
 // quadratic ones, so the tile needs 9K (not 9K + 3 M KM) inverse rows.
 // Blocks per SM: as many as shared memory and registers (about 56 per thread
-// on tetrahedra, 66 on hexahedra, 86 at stencil size 26, measured with ptxas)
-// allow; the kernel's launch bounds ask the compiler for that count.
-template <int K, int M, int KM>
+// on tetrahedra, 66 on hexahedra, 86 at stencil size 26, 80 paired, measured
+// with ptxas) allow; the kernel's launch bounds ask the compiler for that
+// count.
+template <int K, int M, int KM, bool PAIR = false>
 struct ReconSmemF {
   static_assert(M * KM % 4 == 0 && 3 * M * KM <= 9 * K, "record layout");
+  // threads per block: one warp per variable, or (PAIR) three warps, the
+  // first two serving two variables each (0 and 1, 2 and 3), the third one
+  static constexpr int NT = PAIR ? 3 * kRC : kRThreads;
   static constexpr int R0 = 9 * K, R1 = M * 3 * KM;  // quadratic and linear rows
   static constexpr int RG = R0;                       // row of the first second moment
   static constexpr int RP = R0 + 7;                   // first row of sub-stencil positions
@@ -331,7 +344,7 @@ struct ReconSmemF {
   static constexpr size_t nbr = sizeof(float) * 5 * K * kRC;     // neighbour states [5][K][kRC]
   // blocks per SM: 228 KB of shared memory, 1 KB reserved per block; registers
   static constexpr int fit(size_t b) { return (int)(233472 / (b + 1024)); }
-  static constexpr int reg_cap = 65536 / (kRThreads * (M == 4 ? 56 : (K <= 24 ? 66 : 86)));
+  static constexpr int reg_cap = 65536 / (NT * (PAIR ? 80 : (M == 4 ? 56 : (K <= 24 ? 66 : 86))));
   static constexpr int cap(int b) { return b < reg_cap ? b : reg_cap; }
   static constexpr bool phased = cap(fit(head + nbr)) > cap(fit(rec + nbr));
   static constexpr size_t tile = phased ? head : rec;
@@ -420,6 +433,57 @@ __device__ __forceinline__ void rs_linear(const float* tile, const float* snbr, 
   }
 }
 
+// rs_quadratic and rs_linear for two variables va, vb of one cell (own
+// states qa, qb): each tile row is read once and feeds both variables'
+// chains in one packed binary32 FMA (two independent round-to-nearest FMAs:
+// the results of the one-variable forms, in their order).
+template <int K>
+__device__ __forceinline__ void rs_quadratic2(const float* tile, const float* snbr, float qa, float qb, int va,
+                                              int vb, int lane, float a[9], float a2[9]) {
+  auto row = [&](int r) -> float { return tile[r * kRC + lane]; };
+  float2 dq[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    dq[k] = make_float2(snbr[(va * K + k) * kRC + lane] - qa, snbr[(vb * K + k) * kRC + lane] - qb);
+#pragma unroll
+  for (int d = 0; d < 9; ++d) {
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const float x = row(d * K + k);
+      acc = __ffma2_rn(make_float2(x, x), dq[k], acc);
+    }
+    a[d] = acc.x;
+    a2[d] = acc.y;
+  }
+}
+
+template <int K, int M, int KM, int LB>
+__device__ __forceinline__ void rs_linear2(const float* tile, const float* snbr, const uint8_t* ssub, float qa,
+                                           float qb, int va, int vb, int lane, float b[M][3], float b2[M][3]) {
+  auto row = [&](int r) -> float { return tile[r * kRC + lane]; };
+#pragma unroll
+  for (int s = 0; s < M; ++s) {
+    float2 x[KM];
+#pragma unroll
+    for (int r = 0; r < KM; ++r) {
+      const int k = ssub[(s * KM + r) * kRC + lane];
+      x[r] = make_float2(snbr[(va * K + k) * kRC + lane] - qa, snbr[(vb * K + k) * kRC + lane] - qb);
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int r = 0; r < KM; ++r) {
+        const float y = row(LB + (s * 3 + d) * KM + r);
+        acc = __ffma2_rn(make_float2(y, y), x[r], acc);
+      }
+      b[s][d] = acc.x;
+      b2[s][d] = acc.y;
+    }
+  }
+}
+
 // Bytes [off, off + len) of a block's record (rec) to shared memory at dst,
 // completing on bar; called by warp 0.
 __device__ __forceinline__ void rec_copy(unsigned char* dst, const char* rec, size_t off, size_t len, uint64_t* bar) {
@@ -439,19 +503,23 @@ __device__ __forceinline__ void rec_copy(unsigned char* dst, const char* rec, si
 // mbarrier (initialised, count 1); phase: the parity of bar's next phase,
 // advanced by each copy this call waits for.  Returns false, with
 // FLAG_TIMEOUT set, if a copy did not land within the bounded wait.
-template <int K, int M, int KM, bool COH = false>
+template <int K, int M, int KM, bool COH = false, bool PAIR = false>
 __device__ __forceinline__ bool recon_rs_block(const DevMesh& m, const DevParams& P, const float* __restrict__ Qf,
                                                float* __restrict__ coef, Control* __restrict__ ctl, int64_t c0,
                                                unsigned char* smem_raw, uint64_t* bar, uint32_t& phase) {
-  using S = ReconSmemF<K, M, KM>;
+  using S = ReconSmemF<K, M, KM, PAIR>;
+  constexpr int NW = S::NT / 32;  // warps
   float* tile = reinterpret_cast<float*>(smem_raw);                  // [rows][kRC]
   const uint8_t* ssub = smem_raw + (size_t)S::RP * 128;              // [M*KM][kRC]
   float* snbr = reinterpret_cast<float*>(smem_raw + S::tile);        // [5][K][kRC]
   const char* rec = reinterpret_cast<const char*>(m.rec32) + (size_t)(c0 / kRC) * S::rec;
   const int64_t nc = m.nc;
-  const int t = threadIdx.x, lane = t & 31, v = t >> 5;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int nv = nc - c0 < kRC ? (int)(nc - c0) : kRC;  // cells of this block
   const bool live = lane < nv;
+  // the thread's variable va, and with PAIR in warps 0 and 1 also vb = va + 1
+  const int va = PAIR ? 2 * w : w, vb = va + 1;
+  const bool two = PAIR && w < 2;  // uniform over the warp
   // a bounded wait for the copies of the current phase; false: flag, one
   // more bounded wait for the copies in flight, and leave (only a stalled
   // memory system explains a block's own copies, under 40 KB, not landing
@@ -466,29 +534,30 @@ __device__ __forceinline__ bool recon_rs_block(const DevMesh& m, const DevParams
     return ok;
   };
   // 1. the block's record (the head only, phased)
-  if (v == 0) rec_copy(smem_raw, rec, 0, S::tile, bar);
+  if (w == 0) rec_copy(smem_raw, rec, 0, S::tile, bar);
   // 2. stencil neighbours' states and the cell's own (overlap the copies).
-  // Thread (v, lane) fetches entries k = v, v + 5, ... of column `lane`.
-  constexpr int NE = (K + 4) / 5;
+  // Thread (w, lane) fetches entries k = w, w + NW, ... of column `lane`.
+  constexpr int NE = (K + NW - 1) / NW;
   int32_t jn[NE];
 #pragma unroll
   for (int i = 0; i < NE; ++i) {
-    const int k = v + 5 * i;
+    const int k = w + NW * i;
     jn[i] = (k < K && live) ? __ldcs(m.sten + (int64_t)k * nc + c0 + lane) : 0;
   }
-  const float qv = live ? ldro<COH>(Qf + 8 * (c0 + lane) + v) : 0.f;
+  const float qv = live ? ldro<COH>(Qf + 8 * (c0 + lane) + va) : 0.f;
+  const float qv2 = (two && live) ? ldro<COH>(Qf + 8 * (c0 + lane) + vb) : 0.f;
   float4 qa[NE];
   float qb[NE];
 #pragma unroll
   for (int i = 0; i < NE; ++i) {
-    if (v + 5 * i < K && live) {
+    if (w + NW * i < K && live) {
       qa[i] = ldro<COH>(reinterpret_cast<const float4*>(Qf + 8 * (int64_t)jn[i]));
       qb[i] = ldro<COH>(Qf + 8 * (int64_t)jn[i] + 4);
     }
   }
 #pragma unroll
   for (int i = 0; i < NE; ++i) {
-    const int k = v + 5 * i;
+    const int k = w + NW * i;
     if (k < K && live) {
       float* dst = snbr + k * kRC + lane;
       dst[0] = qa[i].x;
@@ -500,38 +569,55 @@ __device__ __forceinline__ bool recon_rs_block(const DevMesh& m, const DevParams
   }
   // 3. the copies have landed and the neighbour states are in place
   if (!landed()) return false;
-  float a[9], b[M][3];
-  if (live) rs_quadratic<K, M>(tile, snbr, qv, v, lane, a);
+  float a[9], b[M][3], a2[9], b2[M][3];
+  if (live) {
+    if (two) rs_quadratic2<K>(tile, snbr, qv, qv2, va, vb, lane, a, a2);
+    else rs_quadratic<K, M>(tile, snbr, qv, va, lane, a);
+  }
   if constexpr (S::phased) {
     __syncthreads();  // every warp has read its quadratic rows
-    if (v == 0) rec_copy(smem_raw, rec, S::head, S::rec - S::head, bar);
+    if (w == 0) rec_copy(smem_raw, rec, S::head, S::rec - S::head, bar);
     if (!landed()) return false;
   }
-  float res[10];
+  float res[10], res2[10];
   if (live) {
-    rs_linear<K, M, KM, S::LB>(tile, snbr, ssub, qv, v, lane, b);
+    if (two) rs_linear2<K, M, KM, S::LB>(tile, snbr, ssub, qv, qv2, va, vb, lane, b, b2);
+    else rs_linear<K, M, KM, S::LB>(tile, snbr, ssub, qv, va, lane, b);
     float mi[6];
 #pragma unroll
     for (int q = 0; q < 6; ++q) mi[q] = tile[(S::RG + q) * kRC + lane];
     const float hi = tile[(S::RG + 6) * kRC + lane];
     const float glin = P.f_glin, g0 = 1.f - float(M) * glin, eps = P.f_eps;
     recon_finish<float, M>(a, b, qv, mi, hi, glin, g0, eps, res);
+    if (two) recon_finish<float, M>(a2, b2, qv2, mi, hi, glin, g0, eps, res2);
   }
-  write_block_records<float>(tile, res, live, lane, v, nv, coef, c0);
+  __syncthreads();  // every warp is done with the tile
+  if (live) {
+    stage_record<float>(tile, res, lane, va);
+    if (two) stage_record<float>(tile, res2, lane, vb);
+  }
+  flush_records<float, S::NT>(tile, nv, coef, c0);
   return true;
 }
 
-template <int K, int M, int KM>
-__global__ void __launch_bounds__(kRThreads, ReconSmemF<K, M, KM>::blocks) k_recon_rs(DevMesh m, DevParams P,
-                                                                                 const float* __restrict__ Qf,
-                                                        float* __restrict__ coef, Control* __restrict__ ctl) {
+// Paired variables (three warps) on tetrahedra, measured: the 48^3 x 6
+// reconstruction 0.325 against 0.359 ms per step (80 registers, 8 blocks of
+// 96 per SM); on hexahedra the pairs need 110 registers and run 10% (K = 24
+// shell) and 14% (K = 26 hybrid shell) slower, so they keep one warp per
+// variable.
+template <int M>
+constexpr bool recon_pair() { return M == 4; }
+template <int K, int M, int KM, bool PAIR>
+__global__ void __launch_bounds__(ReconSmemF<K, M, KM, PAIR>::NT, ReconSmemF<K, M, KM, PAIR>::blocks)
+    k_recon_rs(DevMesh m, DevParams P, const float* __restrict__ Qf, float* __restrict__ coef,
+               Control* __restrict__ ctl) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
   if (m.nmesh == 1 && ctl->dt == 0.0) return;  // uniform over the grid (a batch computes every member)
   if (threadIdx.x == 0) mbar_init(&bar, 1);
   __syncthreads();
   uint32_t phase = 0;
-  recon_rs_block<K, M, KM>(m, P, Qf, coef, ctl, (int64_t)blockIdx.x * kRC, smem_raw, &bar, phase);
+  recon_rs_block<K, M, KM, false, PAIR>(m, P, Qf, coef, ctl, (int64_t)blockIdx.x * kRC, smem_raw, &bar, phase);
 }
 
 }  // namespace

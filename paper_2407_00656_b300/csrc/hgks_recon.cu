@@ -14,15 +14,16 @@ void recon_launch(const DevMesh& m, const DevParams& p, const QT* Q, Real* coef,
   using S = ReconSmem<Real, K, M, KM>;
   const unsigned nb = (unsigned)((m.nc + kRC - 1) / kRC);
   if constexpr (sizeof(Real) == 4) {
-    using SF = ReconSmemF<K, M, KM>;
+    constexpr bool PAIR = recon_pair<M>();
+    using SF = ReconSmemF<K, M, KM, PAIR>;
     if (prep) {
       cudaFuncSetAttribute(k_recon<Real, QT, K, M, KM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)S::bytes);
-      cudaFuncSetAttribute(k_recon_rs<K, M, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SF::bytes);
+      cudaFuncSetAttribute(k_recon_rs<K, M, KM, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SF::bytes);
       return;
     }
     if (p.recon_variant == 1) k_recon<Real, QT, K, M, KM, true><<<nb, kRThreads, S::bytes, s>>>(m, p, Q, coef, ctl);
-    else k_recon_rs<K, M, KM><<<nb, kRThreads, SF::bytes, s>>>(m, p, Q, coef, ctl);
+    else k_recon_rs<K, M, KM, PAIR><<<nb, SF::NT, SF::bytes, s>>>(m, p, Q, coef, ctl);
   } else {
     if (prep) {
       cudaFuncSetAttribute(k_recon<Real, QT, K, M, KM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
