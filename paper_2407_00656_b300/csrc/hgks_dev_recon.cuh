@@ -351,6 +351,18 @@ struct ReconSmemF {
   static constexpr size_t bytes = tile + nbr;
   static constexpr int blocks = cap(fit(bytes));
   static constexpr int LB = phased ? 0 : RL;  // tile row of the first linear row
+  // phased: the quadratic coefficients d < DS read rows 0 .. DS K - 1, which
+  // the linear rows then replace while the coefficients d >= DS are formed
+  // (hexahedra: DS even, for their pairs of rows).  Measured: the K = 24
+  // hexahedral shell's reconstruction 2.7% faster; paired blocks copy after
+  // all nine (DS = 9).
+  static constexpr int ds_min() {
+    int d = 0;
+    while (d * K < R1) ++d;
+    return d;
+  }
+  static constexpr int DS = (!phased || PAIR) ? 9 : (M == 8 ? (ds_min() + 1) / 2 * 2 : ds_min());
+  static_assert(DS * K >= R1 && DS <= 9, "the linear rows fit in the rows already read");
   // copies in pieces of at most 4 KB, one per lane of warp 0
   static constexpr int piece = 4096;
   static_assert(rec % 16 == 0 && (rec + piece - 1) / piece <= 32, "bulk copies of the record");
@@ -360,38 +372,45 @@ struct ReconSmemF {
 // The least-squares polynomials of one (variable, cell) thread from a
 // binary32 tile of inverse rows ([rows][kRC]) and the block's neighbour
 // states snbr ([5][K][kRC]) less the cell's own qv: the quadratic (a, 9
-// coefficients from tile rows 0 .. 9K-1) and the linear ones (b, 3 per
-// sub-stencil from rows LB .. LB + 3 M KM - 1, members at positions ssub).
-// The operation order is that of k_recon.  On hexahedra, pairs of output
-// rows advance together in packed binary32 FMAs (two independent
+// coefficients from tile rows 0 .. 9K-1, in ranges of d so that a phased
+// block can start its second copy part way through) and the linear ones (b,
+// 3 per sub-stencil from rows LB .. LB + 3 M KM - 1, members at positions
+// ssub).  The operation order is that of k_recon.  On hexahedra, pairs of
+// output rows advance together in packed binary32 FMAs (two independent
 // round-to-nearest FMAs per instruction: the same results); measured 8%
 // faster there and 5% slower on tetrahedra.
-template <int K, int M>
-__device__ __forceinline__ void rs_quadratic(const float* tile, const float* snbr, float qv, int v, int lane,
-                                             float a[9]) {
-  auto row = [&](int r) -> float { return tile[r * kRC + lane]; };
-  float dq[K];
+// Stencil differences of variable v of this thread's cell (own state qv).
+template <int K>
+__device__ __forceinline__ void rs_diff(const float* snbr, float qv, int v, int lane, float dq[K]) {
 #pragma unroll
   for (int k = 0; k < K; ++k) dq[k] = snbr[(v * K + k) * kRC + lane] - qv;
+}
+// Quadratic coefficients a[d], D0 <= d < D1, from tile rows d K .. d K + K - 1.
+template <int K, int M, int D0, int D1>
+__device__ __forceinline__ void rs_quad_rows(const float* tile, const float dq[K], int lane, float a[9]) {
+  auto row = [&](int r) -> float { return tile[r * kRC + lane]; };
   if constexpr (M == 8) {
+    static_assert(D0 % 2 == 0, "pairs of rows start at even d");
     float2 dq2[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) dq2[k] = make_float2(dq[k], dq[k]);
 #pragma unroll
-    for (int d = 0; d < 8; d += 2) {
+    for (int d = D0; d + 1 < D1; d += 2) {
       float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
       for (int k = 0; k < K; ++k) acc = __ffma2_rn(make_float2(row(d * K + k), row((d + 1) * K + k)), dq2[k], acc);
       a[d] = acc.x;
       a[d + 1] = acc.y;
     }
-    float sacc = 0.f;
+    if constexpr ((D1 - D0) % 2 == 1) {
+      float sacc = 0.f;
 #pragma unroll
-    for (int k = 0; k < K; ++k) sacc = fmaf(row(8 * K + k), dq[k], sacc);
-    a[8] = sacc;
+      for (int k = 0; k < K; ++k) sacc = fmaf(row((D1 - 1) * K + k), dq[k], sacc);
+      a[D1 - 1] = sacc;
+    }
   } else {
 #pragma unroll
-    for (int d = 0; d < 9; ++d) {
+    for (int d = D0; d < D1; ++d) {
       float sacc = 0.f;
 #pragma unroll
       for (int k = 0; k < K; ++k) sacc += row(d * K + k) * dq[k];
@@ -433,20 +452,23 @@ __device__ __forceinline__ void rs_linear(const float* tile, const float* snbr, 
   }
 }
 
-// rs_quadratic and rs_linear for two variables va, vb of one cell (own
+// rs_quad_rows and rs_linear for two variables va, vb of one cell (own
 // states qa, qb): each tile row is read once and feeds both variables'
 // chains in one packed binary32 FMA (two independent round-to-nearest FMAs:
 // the results of the one-variable forms, in their order).
 template <int K>
-__device__ __forceinline__ void rs_quadratic2(const float* tile, const float* snbr, float qa, float qb, int va,
-                                              int vb, int lane, float a[9], float a2[9]) {
-  auto row = [&](int r) -> float { return tile[r * kRC + lane]; };
-  float2 dq[K];
+__device__ __forceinline__ void rs_diff2(const float* snbr, float qa, float qb, int va, int vb, int lane,
+                                         float2 dq[K]) {
 #pragma unroll
   for (int k = 0; k < K; ++k)
     dq[k] = make_float2(snbr[(va * K + k) * kRC + lane] - qa, snbr[(vb * K + k) * kRC + lane] - qb);
+}
+template <int K, int D0, int D1>
+__device__ __forceinline__ void rs_quad_rows2(const float* tile, const float2 dq[K], int lane, float a[9],
+                                              float a2[9]) {
+  auto row = [&](int r) -> float { return tile[r * kRC + lane]; };
 #pragma unroll
-  for (int d = 0; d < 9; ++d) {
+  for (int d = D0; d < D1; ++d) {
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -569,14 +591,38 @@ __device__ __forceinline__ bool recon_rs_block(const DevMesh& m, const DevParams
   }
   // 3. the copies have landed and the neighbour states are in place
   if (!landed()) return false;
+  constexpr int DS = S::DS;
   float a[9], b[M][3], a2[9], b2[M][3];
-  if (live) {
-    if (two) rs_quadratic2<K>(tile, snbr, qv, qv2, va, vb, lane, a, a2);
-    else rs_quadratic<K, M>(tile, snbr, qv, va, lane, a);
+  if constexpr (PAIR) {
+    static_assert(DS == 9, "paired blocks copy the linear rows after all quadratic rows");
+    if (live) {
+      if (two) {
+        float2 dq[K];
+        rs_diff2<K>(snbr, qv, qv2, va, vb, lane, dq);
+        rs_quad_rows2<K, 0, 9>(tile, dq, lane, a, a2);
+      } else {
+        float dq[K];
+        rs_diff<K>(snbr, qv, va, lane, dq);
+        rs_quad_rows<K, M, 0, 9>(tile, dq, lane, a);
+      }
+    }
+    if constexpr (S::phased) {
+      __syncthreads();  // every warp has read its quadratic rows
+      if (w == 0) rec_copy(smem_raw, rec, S::head, S::rec - S::head, bar);
+    }
+  } else {
+    float dq[K];
+    if (live) {
+      rs_diff<K>(snbr, qv, va, lane, dq);
+      rs_quad_rows<K, M, 0, DS>(tile, dq, lane, a);
+    }
+    if constexpr (S::phased) {
+      __syncthreads();  // every warp has read rows 0 .. DS K - 1
+      if (w == 0) rec_copy(smem_raw, rec, S::head, S::rec - S::head, bar);
+    }
+    if (live) rs_quad_rows<K, M, DS, 9>(tile, dq, lane, a);
   }
   if constexpr (S::phased) {
-    __syncthreads();  // every warp has read its quadratic rows
-    if (w == 0) rec_copy(smem_raw, rec, S::head, S::rec - S::head, bar);
     if (!landed()) return false;
   }
   float res[10], res2[10];
