@@ -60,8 +60,8 @@ ROOF_TABLE = {
 # DRAM bytes per cell of k_recon_rs as built, keyed by stencil shape (K, M,
 # KM), for the traffic of its roofline
 RECON_RS_DRAM = {
-    (14, 4, 6): dict(bytes_per_cell=1120.7, sha="edb183194177", src="ncu DRAM bytes on 48^3 x 6 tets"),
-    (24, 8, 3): dict(bytes_per_cell=1524.4, sha="40834508ffb3", src="ncu DRAM bytes on the 6 x 40^2 x 52 hex shell"),
+    (14, 4, 6): dict(bytes_per_cell=1118.8, sha="f227f2271376", src="ncu DRAM bytes on 48^3 x 6 tets"),
+    (24, 8, 3): dict(bytes_per_cell=1520.6, sha="f227f2271376", src="ncu DRAM bytes on the 6 x 40^2 x 52 hex shell"),
 }
 # Algorithmic bytes per cell of one binary32 reconstruction launch (k_recon_rs):
 # the cell's share of its block's binary32 record (pseudo-inverse rows
