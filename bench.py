@@ -82,7 +82,7 @@ def kernel_source_digest(kernel: str = "k_flux") -> str:
     shared device helpers and its host launcher)."""
     import hashlib
 
-    files = {"k_flux": ("hgks_dev_common.cuh", "hgks_dev_flux.cuh", "hgks_flux.cu"),
+    files = {"k_flux": ("hgks_dev_common.cuh", "erfcx_table.h", "hgks_dev_flux.cuh", "hgks_flux.cu"),
              "k_recon_rs": ("hgks_dev_common.cuh", "hgks_dev_recon.cuh", "hgks_recon.cu")}[kernel]
     h = hashlib.sha256()
     for f in files:

@@ -274,9 +274,15 @@ int hgks_profile(hgks_solver* s, int n_steps, double t_end, double dt_fixed, dou
  * hgks_test_fail_alloc: the library's n-th device allocation from now on
  * (n = 0: the next one) fails as an exhausted memory pool would, so the
  * creating call returns HGKS_ENOMEM and releases what it had taken; n < 0
- * switches the hook off.  Process-wide; returns HGKS_OK. */
+ * switches the hook off.  Process-wide; returns HGKS_OK.
+ * hgks_test_erfcx: y[i] = erfcx(x[i]) = exp(x^2) erfc(x) as the binary64 flux
+ * computes it (its half-line Maxwellian moments, Section 2.1), for x >= 0
+ * or NaN; x and y are host arrays of n values, owned by the caller.
+ * Synchronises.  Errors: HGKS_EINVAL (n < 0, NULL arrays), HGKS_ENOMEM,
+ * HGKS_ECUDA. */
 int hgks_test_barrier_limit(hgks_solver* s, int64_t cycles);
 int hgks_test_fail_alloc(int n);
+int hgks_test_erfcx(const double* x, double* y, int64_t n);
 
 /* Largest n_cells accepted by hgks_cfl_dt_noalloc. */
 #define HGKS_NOALLOC_MAX_CELLS 4194304

@@ -789,6 +789,31 @@ int hgks_test_fail_alloc(int n) {
   return HGKS_OK;
 }
 
+int hgks_test_erfcx(const double* x, double* y, int64_t n) {
+  if (n < 0 || (n > 0 && (!x || !y))) return fail(HGKS_EINVAL, "hgks_test_erfcx: bad arguments");
+  if (n == 0) return HGKS_OK;
+  cudaStream_t st;
+  HGKS_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "cudaStreamCreate");
+  void* d = nullptr;
+  int rc = alloc_on(&d, (size_t)n * 2 * sizeof(double), st, "hgks_test_erfcx");
+  if (rc == HGKS_OK) {
+    double* dx = static_cast<double*>(d);
+    double* dy = dx + n;
+    cudaError_t e = cudaMemcpyAsync(dx, x, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+      hgks::launch_test_erfcx(dx, dy, n, st);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(y, dy, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFreeAsync(d, st);
+    cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "hgks_test_erfcx");
+  }
+  cudaStreamDestroy(st);
+  return rc;
+}
+
 int hgks_tuning(const hgks_solver* s, int* flux_variant, int* recon_variant) {
   if (!s) return fail(HGKS_EINVAL, "NULL solver");
   if (flux_variant) *flux_variant = s->dp.flux_variant;

@@ -150,6 +150,12 @@ __global__ void k_rec32(DevMesh m, float* __restrict__ rec) {
   rec[i] = cvt<float>(x);
 }
 
+// erfcx_tab on n values (test path).
+__global__ void k_test_erfcx(const double* __restrict__ x, double* __restrict__ y, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (i < n) y[i] = erfcx_tab(x[i]);
+}
+
 // Binary32 copy of the state (mixed precision).
 // Caller order and layout ([n][5], member-local index perm[c]) to the internal
 // structure-of-arrays order of cells coff .. coff+n-1, and back.

@@ -209,6 +209,8 @@ void launch_state_out(const DevMesh& m, const double* Q, int64_t coff, int64_t n
 // face geometry (fdl32, fdr32, fn32, fw32) and the reconstruction records
 // (rec32).
 void launch_round32(const DevMesh& m, cudaStream_t s);
+// The binary64 erfcx of the flux on n device values (test path).
+void launch_test_erfcx(const double* x, double* y, int64_t n, cudaStream_t s);
 // L and dL/dt of the current state for step dt into Qs[0:5] and R (as L) -- test path.
 void launch_operator(const DevMesh& m, const DevParams& p, const DevWork& w, int precision, double dt,
                      double* L, double* dL, cudaStream_t s);

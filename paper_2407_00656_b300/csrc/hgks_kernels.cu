@@ -64,6 +64,10 @@ void launch_round32(const DevMesh& m, cudaStream_t s) {
   if (nr > 0) k_rec32<<<blocks(nr), kBlock, 0, s>>>(m, const_cast<float*>(m.rec32));
 }
 
+void launch_test_erfcx(const double* x, double* y, int64_t n, cudaStream_t s) {
+  if (n > 0) k_test_erfcx<<<blocks(n), kBlock, 0, s>>>(x, y, n);
+}
+
 void launch_setdt(const DevMesh& m, const DevWork& w, double dt, cudaStream_t s) {
   k_setdt<<<(m.nmesh + 127) / 128, 128, 0, s>>>(w.ctl, m.nmesh, dt);
 }

@@ -64,7 +64,7 @@ EXPORTS = ("hgks_params_default", "hgks_mesh_create", "hgks_mesh_destroy", "hgks
            "hgks_sync", "hgks_read", "hgks_member_read", "hgks_stage_operator", "hgks_profile", "hgks_solver_bytes",
            "hgks_tuning", "hgks_set_tuning", "hgks_destroy", "hgks_last_error", "hgks_cfl_dt_noalloc",
            "hgks_dmesh_create", "hgks_dmesh_release", "hgks_dmesh_info", "hgks_init_shared",
-           "hgks_test_barrier_limit", "hgks_test_fail_alloc")
+           "hgks_test_barrier_limit", "hgks_test_fail_alloc", "hgks_test_erfcx")
 
 
 def lib():
@@ -109,6 +109,8 @@ def lib():
             L.hgks_test_barrier_limit.restype = C.c_int
             L.hgks_test_fail_alloc.argtypes = [C.c_int]
             L.hgks_test_fail_alloc.restype = C.c_int
+            L.hgks_test_erfcx.argtypes = [dp, dp, C.c_int64]
+            L.hgks_test_erfcx.restype = C.c_int
             L.hgks_cfl_dt_noalloc.argtypes = [vp, vp, C.c_int64, C.POINTER(hgks_params), vp, vp]
             L.hgks_cfl_dt_noalloc.restype = C.c_int
             L.hgks_dmesh_create.argtypes = [vp, vp, C.POINTER(vp)]
@@ -170,6 +172,14 @@ def test_fail_alloc(n: int) -> None:
     """hgks_test_fail_alloc: make the library's n-th device allocation from now
     on fail (n = 0: the next one); n < 0 switches the hook off."""
     _check(lib().hgks_test_fail_alloc(int(n)), "hgks_test_fail_alloc")
+
+
+def test_erfcx(x) -> np.ndarray:
+    """hgks_test_erfcx: the binary64 flux's erfcx on the values x."""
+    x = np.ascontiguousarray(x, dtype=np.float64).ravel()
+    y = np.empty_like(x)
+    _check(lib().hgks_test_erfcx(_dp(x), _dp(y), x.size), "hgks_test_erfcx")
+    return y
 
 
 class Mesh:
