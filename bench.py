@@ -48,20 +48,20 @@ sys.path.insert(0, ROOT)
 # Flops: binary64 2 dfma + dadd + dmul (FP64 path), binary32 2 ffma + fadd +
 # fmul (mixed path), per launch divided by the units of the launch.
 ROOF_TABLE = {
-    ("k_flux", "fp64", 3, False): dict(unit="face", flop=4786, dram=478.5, sha="79e699e45aa6",
+    ("k_flux", "fp64", 3, False): dict(unit="face", flop=4498, dram=478.5, sha="cffb70417c18",
                                        src="ncu operation counts and DRAM bytes on 48^3 x 6 tets"),
-    ("k_flux", "fp64", 4, True): dict(unit="face", flop=13020, dram=541.4, sha="79e699e45aa6",
+    ("k_flux", "fp64", 4, True): dict(unit="face", flop=12636, dram=541.9, sha="cffb70417c18",
                                       src="ncu operation counts and DRAM bytes on the 6 x 40^2 x 52 hex shell"),
-    ("k_flux", "mixed", 3, False): dict(unit="face", flop=4368, dram=247.6, sha="79e699e45aa6",
+    ("k_flux", "mixed", 3, False): dict(unit="face", flop=4368, dram=247.3, sha="cffb70417c18",
                                         src="ncu operation counts and DRAM bytes on 48^3 x 6 tets"),
-    ("k_flux", "mixed", 4, True): dict(unit="face", flop=11739, dram=279.6, sha="79e699e45aa6",
+    ("k_flux", "mixed", 4, True): dict(unit="face", flop=11739, dram=279.0, sha="cffb70417c18",
                                        src="ncu operation counts and DRAM bytes on the 6 x 40^2 x 52 hex shell"),
 }
 # DRAM bytes per cell of k_recon_rs as built, keyed by stencil shape (K, M,
 # KM), for the traffic of its roofline
 RECON_RS_DRAM = {
-    (14, 4, 6): dict(bytes_per_cell=1118.8, sha="f227f2271376", src="ncu DRAM bytes on 48^3 x 6 tets"),
-    (24, 8, 3): dict(bytes_per_cell=1520.6, sha="f227f2271376", src="ncu DRAM bytes on the 6 x 40^2 x 52 hex shell"),
+    (14, 4, 6): dict(bytes_per_cell=1118.7, sha="1f4f31a54f24", src="ncu DRAM bytes on 48^3 x 6 tets"),
+    (24, 8, 3): dict(bytes_per_cell=1520.3, sha="1f4f31a54f24", src="ncu DRAM bytes on the 6 x 40^2 x 52 hex shell"),
 }
 # Algorithmic bytes per cell of one binary32 reconstruction launch (k_recon_rs):
 # the cell's share of its block's binary32 record (pseudo-inverse rows
